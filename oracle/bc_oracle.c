@@ -20,7 +20,8 @@
  * Readings where the paper is silent (each also listed in the design notes):
  *   - Eq. 1 sums ordered pairs s != t; pairs with sigma_st = 0 add nothing.
  *   - sigma is kept exactly (unsigned 128-bit) beside its double value; a
- *     flag is raised when any sigma exceeds 2^53.
+ *     flag is raised when any sigma reaches 2^53, the first count that an
+ *     fp64 sum can no longer certify as exact (2^53 + 1 rounds to 2^53).
  *   - Sampling is with replacement. Draw t (t = 0..T-1) takes the first
  *     64-bit word x0 of Philox4x64-10 (Salmon et al., SC'11) with counter
  *     (t, 0, 0, 0) and key (seed, 0), and picks RV index floor(x0*|RV|/2^64)
@@ -257,7 +258,7 @@ static unsigned brandes_source(const orc_graph *g, orc_ws *ws, int32_t s, int64_
         }
         ws->sigma_x[x] = sx;
         ws->sigma[x] = sd;
-        if (sx > TWO_POW_53) flags |= ORC_FLAG_SIGMA_GT_2_53;
+        if (sx >= TWO_POW_53) flags |= ORC_FLAG_SIGMA_GT_2_53;
     }
     /* Eq. 4, w taken in reverse settle order (deepest first) */
     for (int64_t i = k - 1; i >= 1; i--) {
