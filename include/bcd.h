@@ -1,0 +1,250 @@
+/*
+ * bcd.h - C ABI of the GB300 library for single-vertex betweenness
+ * centrality in directed graphs.
+ *
+ * Method: Chehreghani, Bifet, Abdessalem, "Exact and Approximate Algorithms
+ * for Computing Betweenness Centrality in Directed Graphs".
+ *
+ *   BC(r)      = sum over ordered pairs s != t, both != r, of sigma_st(r) /
+ *                sigma_st (Section 2, Eq. 1); pairs with no path add 0.
+ *   RV(r)      = vertices with a path to r, r excluded (Section 4.1, Def. 1),
+ *                found by one traversal of the reverse graph R(G) from r with
+ *                weights ignored (Def. 2-3, Prop. 2).
+ *   E-BCD      = BC(r) = sum over v in RV(r) of delta_v.(r) (Prop. 1, Eq. 5,
+ *                Algorithm 1); delta by the recursion of Eq. 4.
+ *   A-BCD      = (|RV(r)| / T) * sum over T uniform draws v_t from RV(r) of
+ *                delta_{v_t}.(r) (Algorithm 2; Props. 3-4).
+ *
+ * Conventions for every call:
+ *   - Vertex ids are int32 in [0, n). Arcs are directed. A graph has no
+ *     self-loops and no repeated arcs (Section 2).
+ *   - Scores are raw (not normalised) fp64 sums over ordered pairs.
+ *   - Path counts sigma are fp64 integers; when any sigma reaches 2^53 (the
+ *     first count an fp64 sum cannot certify as exact) the result carries
+ *     BC_FLAG_SIGMA_2_53. That is a flag, not an error.
+ *   - Every call runs on the graph's CUDA stream (bc_graph_desc.stream or
+ *     bc_set_stream) and returns after its results are in host memory.
+ *   - A graph handle may be used by one host thread at a time.
+ *   - On failure a call returns a non-zero bc_status and bc_last_error()
+ *     gives a message for the calling thread.
+ *   - The library allocates and owns its device memory (cudaMalloc); the
+ *     caller's arrays are only read during the call.
+ */
+#ifndef BCD_H
+#define BCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BC_OK = 0,
+    BC_E_INVALID_ARG = 1,      /* a size, id or parameter out of range */
+    BC_E_INVALID_GRAPH = 2,    /* self-loop, repeated or unsorted arc, zero weight */
+    BC_E_OOM = 3,              /* device or host allocation failed */
+    BC_E_CUDA = 4,             /* a CUDA runtime call failed */
+    BC_E_BUFFER_TOO_SMALL = 5, /* output capacity below the needed count */
+    BC_E_TIMEOUT = 6,          /* a bounded device wait gave up */
+    BC_E_INTERNAL = 7
+} bc_status;
+
+typedef enum { BC_MEM_HOST = 0, BC_MEM_DEVICE = 1 } bc_mem_kind;
+
+/* result flags */
+#define BC_FLAG_SIGMA_2_53   0x1u  /* some sigma used for this result is >= 2^53 */
+#define BC_FLAG_TRIVIAL_ZERO 0x2u  /* out-degree(r) = 0: BC(r) = 0 by Prop. 1, no traversal */
+
+/*
+ * Graph description (Section 2). CSR of the forward graph G:
+ *   row_offsets[n+1] int64, non-decreasing, row_offsets[0] = 0,
+ *                    row_offsets[n] = m;
+ *   cols[m]          int32 heads; within each row strictly increasing
+ *                    (sorted, which also rules out repeated arcs), no
+ *                    self-loop;
+ *   weights[m]       uint32 positive arc lengths, or NULL for an
+ *                    unweighted graph (every arc has length 1).
+ * mem_kind tells whether the three pointers are host or device memory.
+ * stream is a cudaStream_t (NULL: the legacy default stream).
+ */
+typedef struct {
+    int32_t n;
+    int64_t m;
+    const int64_t *row_offsets;
+    const int32_t *cols;
+    const uint32_t *weights;
+    int32_t mem_kind;
+    void *stream;
+} bc_graph_desc;
+
+typedef struct bc_graph bc_graph;
+
+/*
+ * Copies the graph to the device, validates it and builds the reverse
+ * graph R(G) there (Section 4.1, Def. 2). The caller keeps ownership of its
+ * arrays. Errors: BC_E_INVALID_ARG (n <= 0, m < 0, NULL pointer, offsets
+ * not monotone, head out of range), BC_E_INVALID_GRAPH (self-loop, row not
+ * strictly increasing, weight 0), BC_E_OOM, BC_E_CUDA. *out is set only on
+ * success.
+ */
+bc_status bc_graph_create(const bc_graph_desc *desc, bc_graph **out);
+
+/* Frees every device and host resource of the handle. NULL is allowed. */
+void bc_graph_destroy(bc_graph *g);
+
+/* Sets the CUDA stream (cudaStream_t) used by later calls on g. */
+bc_status bc_set_stream(bc_graph *g, void *stream);
+
+/* n, m and whether the graph carries weights (any pointer may be NULL). */
+bc_status bc_graph_info(const bc_graph *g, int32_t *n, int64_t *m, int32_t *weighted);
+
+/*
+ * Copies R(G) out to host arrays: roffsets[n+1], rcols[m] and, for a
+ * weighted graph, rweights[m] (may be NULL). Row order within a row is
+ * unspecified (R(G) is a set of arcs; Def. 2).
+ */
+bc_status bc_graph_reverse(const bc_graph *g, int64_t *roffsets, int32_t *rcols, uint32_t *rweights);
+
+/*
+ * RV(r) (Section 4.1): ids of every vertex with a path to r, r excluded,
+ * ascending, written to the host array out[cap]. *count receives |RV(r)|.
+ * If cap < |RV(r)| nothing is written and BC_E_BUFFER_TOO_SMALL is
+ * returned with *count set (call with out = NULL, cap = 0 to size it).
+ */
+bc_status bc_rv_compute(bc_graph *g, int32_t r, int32_t *out, int64_t cap, int64_t *count);
+
+/* Per-query report. Times are milliseconds of device work per phase. */
+typedef struct {
+    int64_t rv_size;          /* |RV(r)| (0 when BC_FLAG_TRIVIAL_ZERO) */
+    int64_t samples;          /* T for sampled queries, 0 for exact */
+    int64_t sources_run;      /* distinct single-source passes this query used */
+    int64_t edges_traversed;  /* sum over those sources s of |E_s|, the arcs whose
+                                 tail s reaches (forward pass, counted once) */
+    int32_t max_level;        /* deepest SPD level met (unweighted) */
+    uint32_t flags;           /* BC_FLAG_* */
+    double ms_rv, ms_sample, ms_spd, ms_total;
+} bc_info;
+
+/*
+ * E-BCD (Algorithm 1): exact BC(r). Zero without any traversal when
+ * out-degree(r) = 0 (Prop. 1). info may be NULL.
+ */
+bc_status bc_exact(bc_graph *g, int32_t r, double *bc, bc_info *info);
+
+/*
+ * A-BCD (Algorithm 2) with T = ceil(ln(2/delta) / (2 eps^2)) samples, i.e.
+ * Eq. "samplesnumber" with eps relative to the range K*|RV(r)| of one
+ * estimate (then |bc - BC(r)| <= eps*K*|RV(r)| with probability >=
+ * 1 - delta, Prop. 4). Requires eps > 0 and 0 < delta < 1.
+ * Draw t (t = 0..T-1) is RV index floor(x0 * |RV(r)| / 2^64) of the
+ * ascending RV(r) list, x0 the first word of Philox4x64-10 with counter
+ * (t, 0, 0, 0) and key (seed, 0). Sampling is with replacement.
+ */
+bc_status bc_approx(bc_graph *g, int32_t r, double eps, double delta, uint64_t seed,
+                    double *bc, bc_info *info);
+
+/* A-BCD with an explicit sample count T >= 1 (the paper's fixed tau runs). */
+bc_status bc_approx_T(bc_graph *g, int32_t r, int64_t T, uint64_t seed, double *bc, bc_info *info);
+
+/* T for (eps, delta) as bc_approx computes it. */
+bc_status bc_samples_for(double eps, double delta, int64_t *T);
+
+/*
+ * The T draws v_t of bc_approx_T(r, T, seed), in draw order, written to
+ * the host array out[T]; *rv_size receives |RV(r)|. When out-degree(r) = 0
+ * or RV(r) is empty no draw is made and *rv_size is 0.
+ */
+bc_status bc_draw_samples(bc_graph *g, int32_t r, int64_t T, uint64_t seed, int32_t *out,
+                          int64_t *rv_size);
+
+typedef enum {
+    BC_QUERY_EXACT = 0,     /* Algorithm 1 */
+    BC_QUERY_APPROX = 1,    /* Algorithm 2, T from (eps, delta) */
+    BC_QUERY_APPROX_T = 2,  /* Algorithm 2, T given */
+    BC_QUERY_HYBRID = 3     /* Section 5 procedure: exact if |RV(r)| <= T, else
+                               Algorithm 2 with T samples */
+} bc_query_kind;
+
+typedef struct {
+    int32_t r;
+    int32_t kind;     /* bc_query_kind */
+    double eps;       /* APPROX */
+    double delta;     /* APPROX */
+    int64_t T;        /* APPROX_T, HYBRID (tau) */
+    uint64_t seed;    /* APPROX, APPROX_T, HYBRID */
+} bc_query;
+
+typedef struct {
+    double bc;
+    int32_t status;   /* bc_status of this query */
+    uint32_t flags;   /* BC_FLAG_* */
+    int64_t rv_size;
+    int64_t samples;  /* T used (0 for an exact answer) */
+} bc_result;
+
+typedef struct {
+    int64_t queries;
+    int64_t sources_run;      /* distinct sources over all queries (set version,
+                                 Section 4.2: one SPD per vertex of the union) */
+    int64_t edges_traversed;  /* sum over those sources of |E_s| */
+    int64_t launches;         /* kernel launches issued */
+    double ms_rv, ms_sample, ms_spd, ms_total;
+} bc_batch_info;
+
+/*
+ * Many queries at once (the set version of Section 4.2): one RV traversal
+ * per group of up to 64 queries, then one single-source pass per vertex of
+ * the union of their source sets, shared by every query that needs it.
+ * out[nq] receives one result per query, each identical (within fp64
+ * summation order) to the single-query call. Returns BC_OK when every
+ * query was attempted; per-query failures are in out[i].status.
+ * info may be NULL.
+ */
+bc_status bc_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out,
+                   bc_batch_info *info);
+
+/*
+ * Parity probe: runs the single-source passes for up to 64 distinct
+ * sources (one tile of the batched kernel) and returns, for each source
+ * i and vertex v, dist[i*n + v] (UINT64_MAX when unreached; hop count for
+ * an unweighted graph) and sigma[i*n + v] (fp64), and for each target
+ * vertex t_j, dep[i*nt + j] = delta_{s_i}.(t_j) (Eq. 4). Any output may be
+ * NULL. flags (may be NULL) receives BC_FLAG_SIGMA_2_53 per source.
+ * Host arrays.
+ */
+bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const int32_t *targets,
+                       int32_t nt, uint64_t *dist, double *sigma, double *dep, uint32_t *flags);
+
+/*
+ * Tuning of the batched traversal (no effect on results beyond fp64
+ * summation order of delta):
+ *   tile_words     mask words per tile: 1, 2 or 4 (64, 128 or 256 sources
+ *                  advanced together);
+ *   chunk_arcs     arcs per unit of work when a vertex's row is split
+ *                  (32..65536, a multiple of 32);
+ *   block_threads  threads per block of the persistent kernel (128..512,
+ *                  a multiple of 32).
+ * Zero fields keep their current value.
+ */
+typedef struct {
+    int32_t tile_words;
+    int32_t chunk_arcs;
+    int32_t block_threads;
+    int32_t reserved;
+} bc_config;
+
+bc_status bc_set_config(bc_graph *g, const bc_config *cfg);
+bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *bc_last_error(void);
+
+/* Version string of the library. */
+const char *bc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCD_H */

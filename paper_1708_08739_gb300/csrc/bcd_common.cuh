@@ -1,0 +1,236 @@
+// Internal declarations shared by the CUDA translation units of libbcd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "bcd.h"
+
+namespace bcd {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// device error codes written to Counters::err
+enum DevErr : int32_t {
+    kDevOk = 0,
+    kDevHistOverflow = 1,
+    kDevChunkOverflow = 2,
+    kDevSlotOverflow = 3,
+    kDevTimeout = 4,
+    kDevLevelOverflow = 5,
+};
+
+// Per-launch control block of the persistent traversal kernel.
+struct Counters {
+    int32_t err;
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    uint32_t pad0;
+    unsigned long long edges;      // sum over reached (v, s) of out-degree(v)
+    unsigned long long pslots;     // partial-row slots handed out this tile
+    unsigned long long levels_max; // deepest level met over all tiles
+    unsigned long long pad1;
+};
+
+// Traversal modes of the persistent kernel.
+enum TravMode : int32_t {
+    kModeReach = 0,  // masks only (RV on R(G)); no sigma, no backward
+    kModeSpd = 1,    // sigma forward, dependency backward
+};
+
+// Flags of a traversal launch.
+enum TravFlags : int32_t {
+    kFlagNoBackward = 1,   // stop after the forward pass
+    kFlagNoReset = 2,      // leave the dense state dirty (probe export)
+    kFlagFullBackward = 4, // backward down to level 0 for every source
+};
+
+struct TravParams {
+    int32_t n;
+    int32_t mode;
+    int32_t flags;
+    int32_t chunk_arcs;
+    const int64_t *off;
+    const int32_t *col;
+    // dense per-vertex state
+    uint64_t *vs;       // [n * vs_stride]: vis[W], dm0[W], dm1[W] (+pad)
+    int32_t vs_stride;  // words per vertex
+    int32_t pad0;
+    int32_t *tag;       // [n] last level a vertex was appended at, -1 none
+    double *sigma;      // [n * S] sigma, then c = (1 + delta) / sigma in place
+    // level history
+    int32_t *hv;        // [hcap]
+    uint64_t *hm;       // [hcap * W]
+    int64_t *hslot;     // [hcap]
+    int64_t hcap;
+    int4 *chunks;       // [ccap] {v, k, nch, e}
+    int64_t ccap;
+    double *partial;    // [pcap * S]
+    int32_t *pdone;     // [pcap]
+    int64_t pcap;
+    unsigned long long *lev_cnt;   // [maxlev + 2]
+    unsigned long long *lev_ccnt;  // [maxlev + 2]
+    int64_t *lev_start;            // [maxlev + 2]
+    int64_t *lev_cstart;           // [maxlev + 2]
+    int32_t maxlev;
+    int32_t pad1;
+    // tiles
+    const int32_t *srcs;  // [ntiles * S], -1 pads the last tile
+    int64_t ntiles;
+    // queries (SPD mode); a group holds at most 64 queries (one mask word)
+    const uint64_t *qmask;   // [n] bit q set at vertex r_q
+    const uint64_t *need;    // [n] bit q set when query q uses the vertex as a source
+    uint64_t exact_q;        // queries whose multiplicity is the need bit
+    const uint32_t *mult;    // [ntiles * S * 64] draw counts of sampled queries, or NULL
+    int32_t *qlevel;         // [S * 64]
+    double *dep;             // [S * 64]
+    double *tile_partial;    // [ntiles * 64]
+    uint32_t *qflags;        // [64]
+    uint64_t *srcflag;       // [W] sigma >= 2^53 seen for a source slot (this tile)
+    // reach mode output
+    uint64_t *rvmask;        // [n]
+    Counters *ctr;
+    double timeout_ns;
+};
+
+}  // namespace bcd
+
+// ---------------------------------------------------------------------------
+// Library internals shared across translation units
+// ---------------------------------------------------------------------------
+
+struct bcd_workspace {
+    int W = 0;           // mask words per tile (S = 64 W sources)
+    int64_t n = 0;
+    int64_t m = 0;
+    // dense state
+    uint64_t *vs = nullptr;
+    int vs_stride = 0;
+    int32_t *tag = nullptr;
+    double *sigma = nullptr;
+    // history
+    int32_t *hv = nullptr;
+    uint64_t *hm = nullptr;
+    int64_t *hslot = nullptr;
+    int64_t hcap = 0;
+    int4 *chunks = nullptr;
+    int64_t ccap = 0;
+    double *partial = nullptr;
+    int32_t *pdone = nullptr;
+    int64_t pcap = 0;
+    unsigned long long *lev_cnt = nullptr;
+    unsigned long long *lev_ccnt = nullptr;
+    int64_t *lev_start = nullptr;
+    int64_t *lev_cstart = nullptr;
+    int32_t maxlev = 0;
+    // per-group state
+    uint64_t *rvmask = nullptr;   // [n]
+    uint64_t *need = nullptr;     // [n]
+    uint64_t *qmask = nullptr;    // [n]
+    int32_t *posd = nullptr;      // [n] position of a vertex in the source union
+    int32_t *dlist = nullptr;     // [n + 64*4] source union, padded to whole tiles
+    int32_t *qlevel = nullptr;    // [256 * 64]
+    double *dep = nullptr;        // [256 * 64]
+    uint32_t *qflags = nullptr;   // [64]
+    uint64_t *srcflag = nullptr;  // [4]
+    bcd::Counters *ctr = nullptr;
+    int64_t *scratch64 = nullptr; // [scratch_len + 256] scan/compaction scratch, counts past scratch_len
+    int64_t scratch_len = 0;
+    uint64_t *small = nullptr;    // [kSmallWords] tables staged from the host for one group
+    // growable
+    double *tile_partial = nullptr;
+    int64_t tile_partial_cap = 0;
+    uint32_t *mult = nullptr;
+    int64_t mult_cap = 0;
+    int32_t *rvlists = nullptr;
+    int64_t rvlists_cap = 0;
+    int32_t *draws = nullptr;
+    int64_t draws_cap = 0;
+    int64_t *blocksums = nullptr;
+    int64_t blocksums_cap = 0;
+    // host pinned staging
+    void *pinned = nullptr;
+    size_t pinned_cap = 0;
+};
+
+// Layout of bcd_workspace::small (64-bit words).
+constexpr int kSmallWords = 4096;
+constexpr int kSmallTable = 0;    // 64 words: slot -> query bits, or per-query scale
+constexpr int kSmallOut = 64;     // 64 words: per-slot counts, or per-query sums
+constexpr int kSmallBits = 128;   // 64 words: (vertex, bit) pairs to set/clear
+constexpr int kSmallBits2 = 192;  // 64 words: (vertex, bit) pairs (query vertices)
+constexpr int kSmallSpecs = 256;  // up to 64 draw specs of 6 words
+
+struct bc_graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    bool weighted = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int64_t *d_off = nullptr;
+    int32_t *d_col = nullptr;
+    uint32_t *d_w = nullptr;
+    int64_t *d_roff = nullptr;
+    int32_t *d_rcol = nullptr;
+    uint32_t *d_rw = nullptr;
+    std::vector<int64_t> h_off;   // forward offsets (degree checks)
+    std::vector<int64_t> h_roff;  // reverse offsets
+    int tile_words = 1;           // W of the SPD kernel
+    int chunk_arcs = 256;
+    int block_threads = 512;
+    bcd_workspace ws;
+    int64_t launches = 0;
+};
+
+namespace bcd {
+
+// error reporting (thread-local message)
+bc_status set_error(bc_status st, const std::string &msg);
+bc_status cuda_error(cudaError_t e, const char *what);
+
+#define BCD_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return bcd::cuda_error(e_, #call); \
+    } while (0)
+
+#define BCD_TRY(call)                            \
+    do {                                         \
+        bc_status s_ = (call);                   \
+        if (s_ != BC_OK) return s_;              \
+    } while (0)
+
+// workspace management (bcd_query.cu)
+bc_status ensure_workspace(bc_graph *g, int W);
+bc_status grow_history(bc_graph *g);
+void free_workspace(bc_graph *g);
+
+// traversal launcher (bcd_traverse.cu)
+bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out);
+bc_status reset_dense_state(bc_graph *g);
+
+template <typename T>
+bc_status dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(BC_E_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return BC_OK;
+}
+
+template <typename T>
+void dev_free(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+}  // namespace bcd

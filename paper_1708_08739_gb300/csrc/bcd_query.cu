@@ -1,0 +1,894 @@
+// Query preparation and the public query calls:
+//   RV(r) for up to 64 roots at once (reach traversal of R(G), Section 4.1),
+//   source sets (Algorithm 1: all of RV(r); Algorithm 2: T Philox draws),
+//   the union of source sets of a group (set version, Section 4.2) cut into
+//   tiles of S = 64 W sources, the batched SPD/dependency traversal, and the
+//   per-query sums (Eq. 5, and Algorithm 2's |RV|/T scaling).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bcd_common.cuh"
+#include "bcd_scan.cuh"
+
+namespace bcd {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds; each multiplies words 0 and 2 by the
+// round multipliers, mixes the high halves with words 1, 3 and the key, and
+// bumps the key by the Weyl increments.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t philox_x0(uint64_t ctr0, uint64_t key0) {
+    const uint64_t kMul0 = 0xD2E7470EE14C6C93ull, kMul1 = 0xCA5A826395121157ull;
+    const uint64_t kInc0 = 0x9E3779B97F4A7C15ull, kInc1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr0, x1 = 0, x2 = 0, x3 = 0;
+    uint64_t k0 = key0, k1 = 0;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t hi_a = __umul64hi(kMul0, x0), lo_a = kMul0 * x0;
+        const uint64_t hi_b = __umul64hi(kMul1, x2), lo_b = kMul1 * x2;
+        const uint64_t y0 = hi_b ^ x1 ^ k0;
+        const uint64_t y2 = hi_a ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo_b;
+        x2 = y2;
+        x3 = lo_a;
+        k0 += kInc0;
+        k1 += kInc1;
+    }
+    return x0;
+}
+
+// Draw t of query q: index floor(x0 * k / 2^64) into the ascending RV list.
+struct DrawSpec {
+    int64_t first;     // offset of this query's draws in the draw buffer
+    int64_t T;
+    int64_t list_off;  // offset of its RV list
+    int64_t k;         // |RV|
+    uint64_t seed;
+    int32_t bit;       // query bit in the group
+    int32_t pad;
+};
+
+static_assert(sizeof(DrawSpec) == 48, "draw spec layout");
+static_assert(kSmallSpecs + 64 * sizeof(DrawSpec) / 8 <= kSmallWords, "draw specs fit the staging buffer");
+
+__global__ void draw_kernel(const DrawSpec *specs, int nspec, const int32_t *lists, int32_t *draws,
+                            uint64_t *need) {
+    const DrawSpec sp = specs[blockIdx.y];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < sp.T;
+         t += (long long)gridDim.x * blockDim.x) {
+        const uint64_t x0 = philox_x0((uint64_t)t, sp.seed);
+        const uint64_t idx = __umul64hi(x0, (uint64_t)sp.k);
+        const int32_t v = lists[sp.list_off + (long long)idx];
+        draws[sp.first + t] = v;
+        if (need) atomicOr((unsigned long long *)&need[v], 1ull << sp.bit);
+    }
+}
+
+__global__ void mult_kernel(const DrawSpec *specs, const int32_t *draws, const int32_t *posd, uint32_t *mult) {
+    const DrawSpec sp = specs[blockIdx.y];
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < sp.T;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int32_t v = draws[sp.first + t];
+        atomicAdd(&mult[(size_t)posd[v] * 64 + sp.bit], 1u);
+    }
+}
+
+// need[v] = OR over slots sl in rvmask[v] of tbl[sl] (exact queries of slot sl)
+__global__ void need_from_rv(const uint64_t *rvmask, int64_t n, const uint64_t *tbl, uint64_t *need) {
+    __shared__ uint64_t s_tbl[64];
+    if (threadIdx.x < 64) s_tbl[threadIdx.x] = tbl[threadIdx.x];
+    __syncthreads();
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        uint64_t x = rvmask[v], o = 0;
+        while (x) {
+            const int b = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            o |= s_tbl[b];
+        }
+        need[v] = o;
+    }
+}
+
+// per-bit population counts of masks[0..n) into cnt[64]
+__global__ void bit_counts(const uint64_t *m, int64_t n, unsigned long long *cnt) {
+    __shared__ unsigned long long s_cnt[64];
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        uint64_t x = m[v];
+        while (x) {
+            const int b = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            atomicAdd(&s_cnt[b], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && s_cnt[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// set (or clear) one bit at a list of vertices
+struct VBit {
+    int32_t v;
+    int32_t bit;
+};
+
+__global__ void set_bits(uint64_t *m, const VBit *list, int cnt, int clear) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const unsigned long long b = 1ull << list[i].bit;
+    if (clear)
+        atomicAnd((unsigned long long *)&m[list[i].v], ~b);
+    else
+        atomicOr((unsigned long long *)&m[list[i].v], b);
+}
+
+__global__ void fill_i32(int32_t *p, int64_t cnt, int32_t val) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+        p[i] = val;
+}
+
+// bc for each query bit: scale[q] * sum over tiles (pairwise, fixed order)
+__global__ void reduce_tiles(const double *tile_partial, int64_t ntiles, const double *scale, double *out) {
+    __shared__ double s[256];
+    const int q = blockIdx.x;
+    double acc = 0.0;
+    // each thread a contiguous run of tiles, then a fixed tree
+    const long long per = (ntiles + blockDim.x - 1) / blockDim.x;
+    const long long t0 = (long long)threadIdx.x * per;
+    const long long t1 = (ntiles < t0 + per) ? ntiles : t0 + per;
+    for (long long t = t0; t < t1; ++t) acc += tile_partial[t * 64 + q];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = s[0] * scale[q];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t pcap) {
+    bcd_workspace &ws = g->ws;
+    dev_free(ws.hv);
+    dev_free(ws.hm);
+    dev_free(ws.hslot);
+    dev_free(ws.chunks);
+    dev_free(ws.partial);
+    dev_free(ws.pdone);
+    if (hcap >= (int64_t)INT32_MAX) hcap = (int64_t)INT32_MAX - 1;
+    ws.hcap = hcap;
+    ws.ccap = ccap;
+    ws.pcap = pcap;
+    BCD_TRY(dev_alloc(&ws.hv, (size_t)hcap));
+    BCD_TRY(dev_alloc(&ws.hm, (size_t)hcap * ws.W));
+    BCD_TRY(dev_alloc(&ws.hslot, (size_t)hcap));
+    BCD_TRY(dev_alloc(&ws.chunks, (size_t)ccap));
+    BCD_TRY(dev_alloc(&ws.partial, (size_t)pcap * 64 * ws.W));
+    BCD_TRY(dev_alloc(&ws.pdone, (size_t)pcap));
+    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)pcap, g->stream));
+    return BC_OK;
+}
+
+bc_status grow_history(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    if (ws.hcap >= (int64_t)INT32_MAX - 1) return set_error(BC_E_OOM, "level history exceeds 2^31 entries");
+    return alloc_history(g, ws.hcap * 2, ws.ccap * 2, ws.pcap * 2);
+}
+
+void free_workspace(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    dev_free(ws.vs);
+    dev_free(ws.tag);
+    dev_free(ws.sigma);
+    dev_free(ws.hv);
+    dev_free(ws.hm);
+    dev_free(ws.hslot);
+    dev_free(ws.chunks);
+    dev_free(ws.partial);
+    dev_free(ws.pdone);
+    dev_free(ws.lev_cnt);
+    dev_free(ws.lev_ccnt);
+    dev_free(ws.lev_start);
+    dev_free(ws.lev_cstart);
+    dev_free(ws.rvmask);
+    dev_free(ws.need);
+    dev_free(ws.qmask);
+    dev_free(ws.posd);
+    dev_free(ws.dlist);
+    dev_free(ws.qlevel);
+    dev_free(ws.dep);
+    dev_free(ws.qflags);
+    dev_free(ws.srcflag);
+    dev_free(ws.ctr);
+    dev_free(ws.scratch64);
+    dev_free(ws.small);
+    dev_free(ws.tile_partial);
+    dev_free(ws.mult);
+    dev_free(ws.rvlists);
+    dev_free(ws.draws);
+    dev_free(ws.blocksums);
+    if (ws.pinned) cudaFreeHost(ws.pinned);
+    ws = bcd_workspace();
+}
+
+bc_status ensure_workspace(bc_graph *g, int W) {
+    bcd_workspace &ws = g->ws;
+    if (ws.W >= W && ws.vs) return BC_OK;
+    free_workspace(g);
+    const int64_t n = g->n, m = g->m;
+    ws.W = W;
+    ws.n = n;
+    ws.m = m;
+    ws.vs_stride = ((3 * W + 3) / 4) * 4;
+    BCD_TRY(dev_alloc(&ws.vs, (size_t)n * ws.vs_stride));
+    BCD_TRY(dev_alloc(&ws.tag, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.sigma, (size_t)n * 64 * W));
+    const int64_t ch = g->chunk_arcs;
+    BCD_TRY(alloc_history(g, 8 * n + 4096, 8 * n + 8 * (m / ch) + 4096, 8 * (m / ch) + 4096));
+    ws.maxlev = (int32_t)std::min<int64_t>(n + 1, (int64_t)INT32_MAX - 4);
+    BCD_TRY(dev_alloc(&ws.lev_cnt, (size_t)ws.maxlev + 2));
+    BCD_TRY(dev_alloc(&ws.lev_ccnt, (size_t)ws.maxlev + 2));
+    BCD_TRY(dev_alloc(&ws.lev_start, (size_t)ws.maxlev + 2));
+    BCD_TRY(dev_alloc(&ws.lev_cstart, (size_t)ws.maxlev + 2));
+    BCD_TRY(dev_alloc(&ws.rvmask, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.need, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.qmask, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.posd, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 256));
+    BCD_TRY(dev_alloc(&ws.qlevel, 256 * 64));
+    BCD_TRY(dev_alloc(&ws.dep, 256 * 64));
+    BCD_TRY(dev_alloc(&ws.qflags, 64));
+    BCD_TRY(dev_alloc(&ws.srcflag, 4));
+    BCD_TRY(dev_alloc(&ws.ctr, 1));
+    ws.scratch_len = scan_scratch_len(n) + 64;
+    BCD_TRY(dev_alloc(&ws.scratch64, (size_t)ws.scratch_len + 256));
+    BCD_TRY(dev_alloc(&ws.small, (size_t)kSmallWords));
+    BCD_TRY(reset_dense_state(g));
+    BCD_CUDA(cudaMemsetAsync(ws.rvmask, 0, sizeof(uint64_t) * (size_t)n, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.need, 0, sizeof(uint64_t) * (size_t)n, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.qmask, 0, sizeof(uint64_t) * (size_t)n, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, g->stream));
+    BCD_CUDA(cudaMallocHost(&ws.pinned, 1 << 20));
+    ws.pinned_cap = 1 << 20;
+    return BC_OK;
+}
+
+template <typename T>
+static bc_status ensure_buf(T **p, int64_t *cap, int64_t need) {
+    if (*cap >= need && *p) return BC_OK;
+    dev_free(*p);
+    *cap = 0;
+    int64_t c = std::max<int64_t>(need, 1024);
+    c = c + c / 4;
+    BCD_TRY(dev_alloc(p, (size_t)c));
+    *cap = c;
+    return BC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// group processing
+// ---------------------------------------------------------------------------
+
+struct GQuery {
+    int64_t idx;     // index in the caller's array
+    int32_t r;
+    int32_t kind;    // bc_query_kind after validation
+    int64_t T;       // samples (APPROX*, HYBRID tau)
+    uint64_t seed;
+    int slot;        // RV slot (distinct root)
+    bool sampled;    // resolved: Algorithm 2
+    int64_t rv;      // |RV(r)|
+};
+
+struct GroupTimes {
+    float rv = 0, sample = 0, spd = 0, total = 0;
+    int64_t sources = 0;
+    unsigned long long edges = 0;
+    int levels = 0;
+};
+
+struct Events {
+    cudaEvent_t e[5];
+    bool ok = false;
+    explicit Events(cudaStream_t s) : stream(s) {
+        ok = true;
+        for (auto &x : e)
+            if (cudaEventCreate(&x) != cudaSuccess) ok = false;
+    }
+    ~Events() {
+        for (auto &x : e) cudaEventDestroy(x);
+    }
+    void rec(int i) {
+        if (ok) cudaEventRecord(e[i], stream);
+    }
+    float ms(int a, int b) {
+        float t = 0;
+        if (ok && cudaEventElapsedTime(&t, e[a], e[b]) == cudaSuccess) return t;
+        return 0;
+    }
+    cudaStream_t stream;
+};
+
+static unsigned grid_for(const bc_graph *g, int64_t work, int threads) {
+    const int64_t b = (work + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)g->num_sms * 16));
+}
+
+// RV for up to 64 distinct roots: rvmask[v] bit sl <=> v in RV(roots[sl]).
+static bc_status reach_roots(bc_graph *g, const std::vector<int32_t> &roots, std::vector<int64_t> &sizes) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int nr = (int)roots.size();
+    BCD_CUDA(cudaMemsetAsync(ws.rvmask, 0, sizeof(uint64_t) * (size_t)g->n, s));
+    std::vector<int32_t> tsrc(64, -1);
+    for (int i = 0; i < nr; ++i) tsrc[i] = roots[i];
+    int32_t *d_tsrc = ws.dlist;  // reused: the union list is built later
+    BCD_CUDA(cudaMemcpyAsync(d_tsrc, tsrc.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeReach;
+    p.flags = 0;
+    p.off = g->d_roff;
+    p.col = g->d_rcol;
+    p.srcs = d_tsrc;
+    p.ntiles = 1;
+    p.rvmask = ws.rvmask;
+    BCD_TRY(run_traversal(g, 1, p, nullptr, nullptr));
+    // r itself is not in RV(r)
+    std::vector<VBit> clr(nr);
+    for (int i = 0; i < nr; ++i) clr[i] = VBit{roots[i], i};
+    VBit *d_clr = (VBit *)(ws.small + kSmallBits);
+    BCD_CUDA(cudaMemcpyAsync(d_clr, clr.data(), sizeof(VBit) * nr, cudaMemcpyHostToDevice, s));
+    set_bits<<<1, 64, 0, s>>>(ws.rvmask, d_clr, nr, 1);
+    unsigned long long *d_cnt = (unsigned long long *)(ws.small + kSmallOut);
+    BCD_CUDA(cudaMemsetAsync(d_cnt, 0, 64 * sizeof(unsigned long long), s));
+    bit_counts<<<grid_for(g, g->n, 256), 256, 0, s>>>(ws.rvmask, g->n, d_cnt);
+    unsigned long long hc[64];
+    BCD_CUDA(cudaMemcpyAsync(hc, d_cnt, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaStreamSynchronize(s));
+    BCD_CUDA(cudaGetLastError());
+    g->launches += 3;
+    sizes.assign(nr, 0);
+    for (int i = 0; i < nr; ++i) sizes[i] = (int64_t)hc[i];
+    return BC_OK;
+}
+
+// Ascending RV lists of the given slots into ws.rvlists; offsets returned.
+static bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::vector<int64_t> &sizes,
+                                std::vector<int64_t> &offs) {
+    bcd_workspace &ws = g->ws;
+    int64_t total = 0;
+    offs.assign(64, -1);
+    for (int sl : slots) {
+        if (offs[sl] >= 0) continue;
+        offs[sl] = total;
+        total += sizes[sl];
+    }
+    BCD_TRY(ensure_buf(&ws.rvlists, &ws.rvlists_cap, total + 1));
+    int64_t *d_cnt = ws.scratch64 + ws.scratch_len;  // 1 spare entry past the scan scratch
+    for (int sl = 0; sl < 64; ++sl) {
+        if (offs[sl] < 0) continue;
+        BCD_TRY(compact_mask(ws.rvmask, sl, g->n, ws.rvlists + offs[sl], nullptr, d_cnt, g->stream, ws.scratch64,
+                             ws.scratch_len));
+        g->launches += 3;
+    }
+    return BC_OK;
+}
+
+static double samples_for(double eps, double delta) { return std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps)); }
+
+// Runs one group of at most 64 queries whose out-degree is positive.
+static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int nq = (int)qs.size();
+    const int W = g->tile_words;
+    const int S = 64 * W;
+    Events ev(s);
+    ev.rec(0);
+    // distinct roots
+    std::vector<int32_t> roots;
+    for (auto &q : qs) {
+        auto it = std::find(roots.begin(), roots.end(), q.r);
+        if (it == roots.end()) {
+            q.slot = (int)roots.size();
+            roots.push_back(q.r);
+        } else {
+            q.slot = (int)(it - roots.begin());
+        }
+    }
+    std::vector<int64_t> sizes;
+    BCD_TRY(reach_roots(g, roots, sizes));
+    ev.rec(1);
+    // resolve kinds, need bits of exact queries
+    uint64_t exact_q = 0;
+    std::vector<uint64_t> tbl(64, 0);
+    std::vector<int> sampled_slots;
+    for (int i = 0; i < nq; ++i) {
+        GQuery &q = qs[i];
+        q.rv = sizes[q.slot];
+        q.sampled = (q.kind == BC_QUERY_APPROX || q.kind == BC_QUERY_APPROX_T ||
+                     (q.kind == BC_QUERY_HYBRID && q.rv > q.T));
+        if (q.sampled && q.rv > 0) {
+            sampled_slots.push_back(q.slot);
+        } else if (!q.sampled) {
+            exact_q |= 1ull << i;
+            tbl[q.slot] |= 1ull << i;
+        }
+    }
+    uint64_t *d_tbl = ws.small + kSmallTable;
+    BCD_CUDA(cudaMemcpyAsync(d_tbl, tbl.data(), 64 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+    need_from_rv<<<grid_for(g, g->n, 256), 256, 0, s>>>(ws.rvmask, g->n, d_tbl, ws.need);
+    g->launches += 1;
+    // sampled queries: RV lists and draws
+    std::vector<DrawSpec> specs;
+    int64_t total_draws = 0;
+    if (!sampled_slots.empty()) {
+        std::vector<int64_t> offs;
+        BCD_TRY(build_rv_lists(g, sampled_slots, sizes, offs));
+        for (int i = 0; i < nq; ++i) {
+            GQuery &q = qs[i];
+            if (!q.sampled || q.rv == 0) continue;
+            DrawSpec d;
+            d.first = total_draws;
+            d.T = q.T;
+            d.list_off = offs[q.slot];
+            d.k = q.rv;
+            d.seed = q.seed;
+            d.bit = i;
+            d.pad = 0;
+            specs.push_back(d);
+            total_draws += q.T;
+        }
+        BCD_TRY(ensure_buf(&ws.draws, &ws.draws_cap, total_draws + 1));
+        DrawSpec *d_specs = (DrawSpec *)(ws.small + kSmallSpecs);
+        BCD_CUDA(cudaMemcpyAsync(d_specs, specs.data(), sizeof(DrawSpec) * specs.size(), cudaMemcpyHostToDevice, s));
+        int64_t maxT = 0;
+        for (auto &d : specs) maxT = std::max(maxT, d.T);
+        dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((maxT + 255) / 256, 4096)), (unsigned)specs.size());
+        draw_kernel<<<grid, 256, 0, s>>>(d_specs, (int)specs.size(), ws.rvlists, ws.draws, ws.need);
+        g->launches += 1;
+    }
+    // union of the source sets, padded to whole tiles
+    int64_t *d_cnt = ws.scratch64 + ws.scratch_len;
+    BCD_TRY(compact_mask(ws.need, -1, g->n, ws.dlist, ws.posd, d_cnt, s, ws.scratch64, ws.scratch_len));
+    g->launches += 3;
+    int64_t nd = 0;
+    BCD_CUDA(cudaMemcpyAsync(&nd, d_cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaStreamSynchronize(s));
+    const int64_t ntiles = (nd + S - 1) / S;
+    if (ntiles * S > nd) {
+        fill_i32<<<1, 256, 0, s>>>(ws.dlist + nd, ntiles * S - nd, -1);
+        g->launches += 1;
+    }
+    if (!specs.empty()) {
+        BCD_TRY(ensure_buf(&ws.mult, &ws.mult_cap, std::max<int64_t>(ntiles, 1) * S * 64));
+        BCD_CUDA(cudaMemsetAsync(ws.mult, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(ntiles, 1) * S * 64, s));
+        DrawSpec *d_specs = (DrawSpec *)(ws.small + kSmallSpecs);
+        BCD_CUDA(cudaMemcpyAsync(d_specs, specs.data(), sizeof(DrawSpec) * specs.size(), cudaMemcpyHostToDevice, s));
+        int64_t maxT = 0;
+        for (auto &d : specs) maxT = std::max(maxT, d.T);
+        dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((maxT + 255) / 256, 4096)), (unsigned)specs.size());
+        mult_kernel<<<grid, 256, 0, s>>>(d_specs, ws.draws, ws.posd, ws.mult);
+        g->launches += 1;
+    }
+    // query vertices
+    std::vector<VBit> qb(nq);
+    for (int i = 0; i < nq; ++i) qb[i] = VBit{qs[i].r, i};
+    VBit *d_qb = (VBit *)(ws.small + kSmallBits2);
+    BCD_CUDA(cudaMemcpyAsync(d_qb, qb.data(), sizeof(VBit) * nq, cudaMemcpyHostToDevice, s));
+    set_bits<<<1, 64, 0, s>>>(ws.qmask, d_qb, nq, 0);
+    BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
+    g->launches += 1;
+    ev.rec(2);
+    // batched SPD + dependencies over all tiles
+    std::vector<double> sums(64, 0.0);
+    std::vector<uint32_t> qflags(64, 0);
+    int levels = 0;
+    unsigned long long edges = 0;
+    if (ntiles > 0) {
+        BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, ntiles * 64));
+        TravParams p;
+        memset(&p, 0, sizeof(p));
+        p.mode = kModeSpd;
+        p.flags = 0;
+        p.off = g->d_off;
+        p.col = g->d_col;
+        p.srcs = ws.dlist;
+        p.ntiles = ntiles;
+        p.qmask = ws.qmask;
+        p.need = ws.need;
+        p.exact_q = exact_q;
+        p.mult = specs.empty() ? nullptr : ws.mult;
+        p.qlevel = ws.qlevel;
+        p.dep = ws.dep;
+        p.tile_partial = ws.tile_partial;
+        p.qflags = ws.qflags;
+        p.srcflag = ws.srcflag;
+        BCD_TRY(run_traversal(g, W, p, &levels, &edges));
+        std::vector<double> scale(64, 1.0);
+        for (int i = 0; i < nq; ++i)
+            if (qs[i].sampled && qs[i].rv > 0) scale[i] = (double)qs[i].rv / (double)qs[i].T;
+        double *d_scale = (double *)(ws.small + kSmallTable);
+        double *d_out = (double *)(ws.small + kSmallOut);
+        BCD_CUDA(cudaMemcpyAsync(d_scale, scale.data(), 64 * sizeof(double), cudaMemcpyHostToDevice, s));
+        reduce_tiles<<<64, 256, 0, s>>>(ws.tile_partial, ntiles, d_scale, d_out);
+        BCD_CUDA(cudaMemcpyAsync(sums.data(), d_out, 64 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        BCD_CUDA(cudaMemcpyAsync(qflags.data(), ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        g->launches += 1;
+    }
+    set_bits<<<1, 64, 0, s>>>(ws.qmask, d_qb, nq, 1);
+    g->launches += 1;
+    ev.rec(3);
+    BCD_CUDA(cudaStreamSynchronize(s));
+    BCD_CUDA(cudaGetLastError());
+    for (int i = 0; i < nq; ++i) {
+        bc_result &o = res[qs[i].idx];
+        o.status = BC_OK;
+        o.bc = sums[i];
+        o.flags = (qflags[i] & 1u) ? BC_FLAG_SIGMA_2_53 : 0u;
+        o.rv_size = qs[i].rv;
+        o.samples = (qs[i].sampled && qs[i].rv > 0) ? qs[i].T : 0;
+    }
+    tm.rv = ev.ms(0, 1);
+    tm.sample = ev.ms(1, 2);
+    tm.spd = ev.ms(2, 3);
+    tm.total = ev.ms(0, 3);
+    tm.sources = nd;
+    tm.edges = edges;
+    tm.levels = levels;
+    return BC_OK;
+}
+
+static bc_status check_graph(bc_graph *g, const char *fn) {
+    if (!g) return set_error(BC_E_INVALID_ARG, std::string(fn) + ": NULL graph");
+    if (g->weighted)
+        return set_error(BC_E_INVALID_ARG, std::string(fn) + ": weighted shortest paths are not supported yet");
+    return ensure_workspace(g, g->tile_words);
+}
+
+static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out, bc_batch_info *info) {
+    if (!g) return set_error(BC_E_INVALID_ARG, "bc_batch: NULL graph");
+    if (nq < 0 || (nq > 0 && (!queries || !out))) return set_error(BC_E_INVALID_ARG, "bc_batch: bad query array");
+    BCD_TRY(check_graph(g, "bc_batch"));
+    const int64_t launches0 = g->launches;
+    bc_batch_info bi;
+    memset(&bi, 0, sizeof(bi));
+    bi.queries = nq;
+    std::vector<GQuery> group;
+    auto flush = [&]() -> bc_status {
+        if (group.empty()) return BC_OK;
+        GroupTimes t;
+        bc_status st = run_group(g, group, out, t);
+        if (st != BC_OK) {
+            for (auto &q : group) out[q.idx].status = st;
+            group.clear();
+            return st;
+        }
+        bi.sources_run += t.sources;
+        bi.edges_traversed += (int64_t)t.edges;
+        bi.ms_rv += t.rv;
+        bi.ms_sample += t.sample;
+        bi.ms_spd += t.spd;
+        bi.ms_total += t.total;
+        group.clear();
+        return BC_OK;
+    };
+    bc_status worst = BC_OK;
+    for (int64_t i = 0; i < nq; ++i) {
+        const bc_query &q = queries[i];
+        bc_result &o = out[i];
+        memset(&o, 0, sizeof(o));
+        if (q.r < 0 || q.r >= g->n) {
+            o.status = set_error(BC_E_INVALID_ARG, "query vertex out of range");
+            continue;
+        }
+        GQuery gq;
+        gq.idx = i;
+        gq.r = q.r;
+        gq.kind = q.kind;
+        gq.seed = q.seed;
+        gq.T = 0;
+        gq.slot = 0;
+        gq.sampled = false;
+        gq.rv = 0;
+        if (q.kind == BC_QUERY_EXACT) {
+        } else if (q.kind == BC_QUERY_APPROX) {
+            if (!(q.eps > 0.0) || !(q.delta > 0.0 && q.delta < 1.0)) {
+                o.status = set_error(BC_E_INVALID_ARG, "approx query needs eps > 0 and 0 < delta < 1");
+                continue;
+            }
+            const double T = samples_for(q.eps, q.delta);
+            if (!(T >= 1.0) || T > 4.0e9) {
+                o.status = set_error(BC_E_INVALID_ARG, "approx query: sample count out of range");
+                continue;
+            }
+            gq.T = (int64_t)T;
+        } else if (q.kind == BC_QUERY_APPROX_T || q.kind == BC_QUERY_HYBRID) {
+            if (q.T < 1 || q.T > 4000000000ll) {
+                o.status = set_error(BC_E_INVALID_ARG, "query T must be in [1, 4e9]");
+                continue;
+            }
+            gq.T = q.T;
+        } else {
+            o.status = set_error(BC_E_INVALID_ARG, "unknown query kind");
+            continue;
+        }
+        // Prop. 1 / Algorithm 1: out-degree 0 => BC(r) = 0 without traversal
+        if (g->h_off[q.r + 1] == g->h_off[q.r]) {
+            o.status = BC_OK;
+            o.bc = 0.0;
+            o.flags = BC_FLAG_TRIVIAL_ZERO;
+            continue;
+        }
+        group.push_back(gq);
+        if (group.size() == 64) {
+            bc_status st = flush();
+            if (st != BC_OK) worst = st;
+        }
+    }
+    bc_status st = flush();
+    if (st != BC_OK) worst = st;
+    bi.launches = g->launches - launches0;
+    if (info) *info = bi;
+    if (worst == BC_E_CUDA || worst == BC_E_OOM || worst == BC_E_TIMEOUT || worst == BC_E_INTERNAL) return worst;
+    return BC_OK;
+}
+
+}  // namespace bcd
+
+using namespace bcd;
+
+extern "C" {
+
+bc_status bc_samples_for(double eps, double delta, int64_t *T) {
+    if (!T) return set_error(BC_E_INVALID_ARG, "bc_samples_for: NULL output");
+    if (!(eps > 0.0) || !(delta > 0.0 && delta < 1.0))
+        return set_error(BC_E_INVALID_ARG, "bc_samples_for: need eps > 0 and 0 < delta < 1");
+    const double t = bcd::samples_for(eps, delta);
+    if (!(t >= 1.0) || t > 4.0e9) return set_error(BC_E_INVALID_ARG, "bc_samples_for: sample count out of range");
+    *T = (int64_t)t;
+    return BC_OK;
+}
+
+bc_status bc_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out, bc_batch_info *info) {
+    return run_batch(g, queries, nq, out, info);
+}
+
+static bc_status single(bc_graph *g, const bc_query &q, double *bc, bc_info *info) {
+    if (!bc) return set_error(BC_E_INVALID_ARG, "NULL result pointer");
+    bc_result r;
+    bc_batch_info bi;
+    BCD_TRY(run_batch(g, &q, 1, &r, &bi));
+    if (r.status != BC_OK) return (bc_status)r.status;
+    *bc = r.bc;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->rv_size = r.rv_size;
+        info->samples = r.samples;
+        info->sources_run = bi.sources_run;
+        info->edges_traversed = bi.edges_traversed;
+        info->flags = r.flags;
+        info->ms_rv = bi.ms_rv;
+        info->ms_sample = bi.ms_sample;
+        info->ms_spd = bi.ms_spd;
+        info->ms_total = bi.ms_total;
+    }
+    return BC_OK;
+}
+
+bc_status bc_exact(bc_graph *g, int32_t r, double *bc, bc_info *info) {
+    bc_query q;
+    memset(&q, 0, sizeof(q));
+    q.r = r;
+    q.kind = BC_QUERY_EXACT;
+    return single(g, q, bc, info);
+}
+
+bc_status bc_approx(bc_graph *g, int32_t r, double eps, double delta, uint64_t seed, double *bc, bc_info *info) {
+    bc_query q;
+    memset(&q, 0, sizeof(q));
+    q.r = r;
+    q.kind = BC_QUERY_APPROX;
+    q.eps = eps;
+    q.delta = delta;
+    q.seed = seed;
+    return single(g, q, bc, info);
+}
+
+bc_status bc_approx_T(bc_graph *g, int32_t r, int64_t T, uint64_t seed, double *bc, bc_info *info) {
+    bc_query q;
+    memset(&q, 0, sizeof(q));
+    q.r = r;
+    q.kind = BC_QUERY_APPROX_T;
+    q.T = T;
+    q.seed = seed;
+    return single(g, q, bc, info);
+}
+
+bc_status bc_rv_compute(bc_graph *g, int32_t r, int32_t *out, int64_t cap, int64_t *count) {
+    if (!g || !count) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: NULL argument");
+    if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: vertex out of range");
+    if (cap < 0 || (cap > 0 && !out)) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: bad output buffer");
+    BCD_TRY(ensure_workspace(g, g->tile_words));
+    std::vector<int64_t> sizes;
+    BCD_TRY(reach_roots(g, std::vector<int32_t>{r}, sizes));
+    *count = sizes[0];
+    if (cap < sizes[0]) return set_error(BC_E_BUFFER_TOO_SMALL, "bc_rv_compute: output capacity below |RV(r)|");
+    std::vector<int64_t> offs;
+    BCD_TRY(build_rv_lists(g, std::vector<int>{0}, sizes, offs));
+    if (sizes[0] > 0)
+        BCD_CUDA(cudaMemcpyAsync(out, g->ws.rvlists, sizeof(int32_t) * (size_t)sizes[0], cudaMemcpyDeviceToHost,
+                                 g->stream));
+    BCD_CUDA(cudaStreamSynchronize(g->stream));
+    return BC_OK;
+}
+
+bc_status bc_draw_samples(bc_graph *g, int32_t r, int64_t T, uint64_t seed, int32_t *out, int64_t *rv_size) {
+    if (!g || !rv_size) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: NULL argument");
+    if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: vertex out of range");
+    if (T < 1 || T > 4000000000ll || !out) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: bad T or output");
+    BCD_TRY(ensure_workspace(g, g->tile_words));
+    *rv_size = 0;
+    if (g->h_off[r + 1] == g->h_off[r]) return BC_OK;
+    std::vector<int64_t> sizes;
+    BCD_TRY(reach_roots(g, std::vector<int32_t>{r}, sizes));
+    if (sizes[0] == 0) return BC_OK;
+    *rv_size = sizes[0];
+    std::vector<int64_t> offs;
+    BCD_TRY(build_rv_lists(g, std::vector<int>{0}, sizes, offs));
+    BCD_TRY(ensure_buf(&g->ws.draws, &g->ws.draws_cap, T + 1));
+    DrawSpec d;
+    d.first = 0;
+    d.T = T;
+    d.list_off = 0;
+    d.k = sizes[0];
+    d.seed = seed;
+    d.bit = 0;
+    d.pad = 0;
+    DrawSpec *d_spec = (DrawSpec *)(g->ws.small + kSmallSpecs);
+    BCD_CUDA(cudaMemcpyAsync(d_spec, &d, sizeof(d), cudaMemcpyHostToDevice, g->stream));
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((T + 255) / 256, 4096)), 1);
+    draw_kernel<<<grid, 256, 0, g->stream>>>(d_spec, 1, g->ws.rvlists, g->ws.draws, nullptr);
+    BCD_CUDA(cudaMemcpyAsync(out, g->ws.draws, sizeof(int32_t) * (size_t)T, cudaMemcpyDeviceToHost, g->stream));
+    BCD_CUDA(cudaStreamSynchronize(g->stream));
+    BCD_CUDA(cudaGetLastError());
+    return BC_OK;
+}
+
+bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const int32_t *targets, int32_t nt,
+                       uint64_t *dist, double *sigma, double *dep, uint32_t *flags) {
+    if (!g || (nsrc > 0 && !sources) || (nt > 0 && !targets))
+        return set_error(BC_E_INVALID_ARG, "bc_spd_probe: NULL argument");
+    if (nsrc < 1 || nsrc > 64 || nt < 0 || nt > 64) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: 1..64 sources, 0..64 targets");
+    BCD_TRY(check_graph(g, "bc_spd_probe"));
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int W = ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
+    const int S = 64 * W;
+    for (int i = 0; i < nsrc; ++i) {
+        if (sources[i] < 0 || sources[i] >= g->n) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: source out of range");
+        for (int j = 0; j < i; ++j)
+            if (sources[j] == sources[i]) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: sources must be distinct");
+    }
+    for (int j = 0; j < nt; ++j)
+        if (targets[j] < 0 || targets[j] >= g->n) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: target out of range");
+    const uint64_t tbits = nt == 64 ? ~0ull : ((1ull << nt) - 1ull);
+    std::vector<int32_t> tsrc(S, -1);
+    for (int i = 0; i < nsrc; ++i) tsrc[i] = sources[i];
+    BCD_CUDA(cudaMemcpyAsync(ws.dlist, tsrc.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+    // need: every source needs every target; qmask: target bits
+    std::vector<VBit> nb, qb;
+    for (int i = 0; i < nsrc; ++i)
+        for (int j = 0; j < nt; ++j) nb.push_back(VBit{sources[i], j});
+    for (int j = 0; j < nt; ++j) qb.push_back(VBit{targets[j], j});
+    VBit *d_nb = nullptr;
+    BCD_TRY(dev_alloc(&d_nb, nb.size() + qb.size() + 1));
+    if (!nb.empty() || !qb.empty())
+        BCD_CUDA(cudaMemcpyAsync(d_nb, nb.empty() ? qb.data() : nb.data(), sizeof(VBit) * nb.size(),
+                                 cudaMemcpyHostToDevice, s));
+    if (!qb.empty())
+        BCD_CUDA(cudaMemcpyAsync(d_nb + nb.size(), qb.data(), sizeof(VBit) * qb.size(), cudaMemcpyHostToDevice, s));
+    BCD_CUDA(cudaMemsetAsync(ws.need, 0, sizeof(uint64_t) * (size_t)g->n, s));
+    if (!nb.empty()) set_bits<<<(unsigned)((nb.size() + 255) / 256), 256, 0, s>>>(ws.need, d_nb, (int)nb.size(), 0);
+    if (!qb.empty()) set_bits<<<1, 64, 0, s>>>(ws.qmask, d_nb + nb.size(), (int)qb.size(), 0);
+    BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, 64));
+    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, s));
+    BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeSpd;
+    p.off = g->d_off;
+    p.col = g->d_col;
+    p.srcs = ws.dlist;
+    p.ntiles = 1;
+    p.qmask = ws.qmask;
+    p.need = ws.need;
+    p.exact_q = tbits;
+    p.qlevel = ws.qlevel;
+    p.dep = ws.dep;
+    p.tile_partial = ws.tile_partial;
+    p.qflags = ws.qflags;
+    p.srcflag = ws.srcflag;
+    bc_status st = BC_OK;
+    if (dist || sigma || flags) {
+        p.flags = kFlagNoBackward | kFlagNoReset;
+        st = run_traversal(g, W, p, nullptr, nullptr);
+        if (st == BC_OK) {
+            // export sigma [v][S] and the level history
+            const size_t n = (size_t)g->n;
+            std::vector<double> sg;
+            if (sigma) {
+                sg.resize(n * S);
+                cudaMemcpyAsync(sg.data(), ws.sigma, sizeof(double) * n * S, cudaMemcpyDeviceToHost, s);
+            }
+            std::vector<unsigned long long> lc(ws.maxlev + 2);
+            cudaMemcpyAsync(lc.data(), ws.lev_cnt, sizeof(unsigned long long) * lc.size(), cudaMemcpyDeviceToHost, s);
+            std::vector<uint64_t> sf(W);
+            cudaMemcpyAsync(sf.data(), ws.srcflag, sizeof(uint64_t) * W, cudaMemcpyDeviceToHost, s);
+            cudaError_t ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) st = cuda_error(ce, "probe export");
+            int64_t total = 0;
+            int levels = 0;
+            while (levels < ws.maxlev + 1 && lc[levels] > 0) total += (int64_t)lc[levels++];
+            std::vector<int32_t> hv(std::max<int64_t>(total, 1));
+            std::vector<uint64_t> hm(std::max<int64_t>(total, 1) * W);
+            if (st == BC_OK && total > 0) {
+                cudaMemcpyAsync(hv.data(), ws.hv, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, s);
+                cudaMemcpyAsync(hm.data(), ws.hm, sizeof(uint64_t) * total * W, cudaMemcpyDeviceToHost, s);
+                ce = cudaStreamSynchronize(s);
+                if (ce != cudaSuccess) st = cuda_error(ce, "probe export");
+            }
+            if (st == BC_OK) {
+                if (dist) std::fill(dist, dist + (size_t)nsrc * n, ~0ull);
+                if (sigma) std::fill(sigma, sigma + (size_t)nsrc * n, 0.0);
+                int64_t e = 0;
+                for (int L = 0; L < levels; ++L) {
+                    for (unsigned long long k = 0; k < lc[L]; ++k, ++e) {
+                        const int32_t v = hv[e];
+                        for (int i = 0; i < nsrc; ++i) {
+                            if ((hm[e * W + (i >> 6)] >> (i & 63)) & 1ull) {
+                                if (dist) dist[(size_t)i * n + v] = (uint64_t)L;
+                                if (sigma) sigma[(size_t)i * n + v] = sg[(size_t)v * S + i];
+                            }
+                        }
+                    }
+                }
+                if (flags)
+                    for (int i = 0; i < nsrc; ++i) flags[i] = ((sf[i >> 6] >> (i & 63)) & 1ull) ? BC_FLAG_SIGMA_2_53 : 0u;
+            }
+        }
+        bc_status st2 = reset_dense_state(g);
+        if (st == BC_OK) st = st2;
+    }
+    if (st == BC_OK && dep) {
+        p.flags = 0;
+        BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, s));
+        st = run_traversal(g, W, p, nullptr, nullptr);
+        if (st == BC_OK) {
+            std::vector<double> hd(256 * 64);
+            BCD_CUDA(cudaMemcpyAsync(hd.data(), ws.dep, sizeof(double) * 256 * 64, cudaMemcpyDeviceToHost, s));
+            BCD_CUDA(cudaStreamSynchronize(s));
+            for (int i = 0; i < nsrc; ++i)
+                for (int j = 0; j < nt; ++j) dep[(size_t)i * nt + j] = hd[i * 64 + j];
+        }
+    }
+    if (!qb.empty()) set_bits<<<1, 64, 0, s>>>(ws.qmask, d_nb + nb.size(), (int)qb.size(), 1);
+    cudaStreamSynchronize(s);
+    dev_free(d_nb);
+    return st;
+}
+
+}  // extern "C"

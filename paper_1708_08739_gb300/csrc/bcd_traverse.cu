@@ -1,0 +1,730 @@
+// Persistent multi-source traversal: the single-source work of Algorithm 1
+// (and Algorithm 2) for S = 64*W sources at once.
+//
+// One cooperative launch walks every tile of S sources. Per tile:
+//   forward  (Section 2): level-synchronous BFS over the forward CSR, one
+//            grid barrier per level. Per vertex the dense state holds the
+//            visited mask and two level-parity masks (bit s: vertex is at the
+//            current / next level for source s). Frontier vertices are pushed
+//            along their out-arcs in chunks of at most chunk_arcs arcs; for
+//            every arc (u, v) the sources newly reaching v are
+//            F(u) & ~(visited(v) | current(v)), and sigma_s(v) += sigma_s(u)
+//            by an fp64 atomic add (sigma are integers, so the sum is exact
+//            in any order while below 2^53).
+//   backward (Eq. 4): levels from the deepest one up to the shallowest level
+//            any query vertex sits at. With c_s(w) = (1 + delta_s(w)) /
+//            sigma_s(w), delta_s(v) = sigma_s(v) * sum over tight out-arcs
+//            (v, w) of c_s(w), a pull over out-arcs in CSR order. Long rows
+//            are split into chunks whose partial sums are combined in chunk
+//            order, so the result does not depend on scheduling.
+// Reach mode (RV(r), Section 4.1) runs the forward pass only, over R(G),
+// with one source slot per query root, and ORs every level mask into rvmask.
+//
+// Every grid barrier wait is bounded; a timeout or a capacity overflow sets
+// Counters::err and all blocks leave.
+#include <cooperative_groups.h>
+
+#include "bcd_common.cuh"
+
+namespace bcd {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_vol(const int32_t *p) { return *(volatile const int32_t *)p; }
+
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long *p) {
+    return *(volatile const unsigned long long *)p;
+}
+
+__device__ __forceinline__ void set_err(Counters *c, int32_t code) { atomicCAS(&c->err, 0, code); }
+
+// Grid-wide barrier for a cooperative launch. Every wait is bounded by
+// timeout_ns of wall time (and a spin cap); on timeout or when another block
+// has flagged an error, returns false and the caller leaves the kernel.
+__device__ bool grid_barrier(Counters *c, uint32_t &gen, double timeout_ns) {
+    __shared__ int s_err;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t nb = gridDim.x;
+        const uint32_t arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == nb - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicExch(&c->bar_gen, gen + 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned long long spins = 0;
+            while (ld_acquire(&c->bar_gen) == gen) {
+                if (ld_vol(&c->err) != 0) break;
+                ++spins;
+                if ((spins & 63) == 0 && (double)(global_ns() - t0) > timeout_ns) {
+                    set_err(c, kDevTimeout);
+                    break;
+                }
+                if (spins > (1ull << 31)) {
+                    set_err(c, kDevTimeout);
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+        gen += 1;
+        s_err = ld_vol(&c->err);
+    }
+    __syncthreads();
+    return s_err == 0;
+}
+
+template <int W>
+__device__ __forceinline__ bool mask_bit(const uint64_t (&m)[W], int s) {
+    return (m[s >> 6] >> (s & 63)) & 1ull;
+}
+
+// Appends the vertices a warp discovered at level L+1 (one entry and nch
+// chunks each), with one pair of counter atomics per warp.
+template <int W, int MODE>
+__device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app, int wv, int wnch,
+                                            long long es1, long long cs1, int lane) {
+    const unsigned am = __ballot_sync(kFull, app);
+    if (am == 0) return;
+    const int rank = __popc(am & ((1u << lane) - 1u));
+    const int ne = __popc(am);
+    int x = app ? wnch : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    const int tot = __shfl_sync(kFull, x, 31);
+    unsigned long long eb = 0, cb = 0;
+    if (lane == 0) {
+        eb = atomicAdd(&p.lev_cnt[L + 1], (unsigned long long)ne);
+        cb = atomicAdd(&p.lev_ccnt[L + 1], (unsigned long long)tot);
+    }
+    eb = __shfl_sync(kFull, eb, 0);
+    cb = __shfl_sync(kFull, cb, 0);
+    if (app) {
+        const long long e = es1 + (long long)eb + rank;
+        const long long c0 = cs1 + (long long)cb + (x - wnch);
+        if (e >= p.hcap) {
+            set_err(p.ctr, kDevHistOverflow);
+        } else if (c0 + wnch > p.ccap) {
+            set_err(p.ctr, kDevChunkOverflow);
+        } else {
+            p.hv[e] = wv;
+            for (int kk = 0; kk < wnch; ++kk) p.chunks[c0 + kk] = make_int4(wv, kk, wnch, (int)e);
+            if (MODE == kModeSpd) {
+                long long sl = -1;
+                if (wnch > 1) {
+                    const unsigned long long b = atomicAdd(&p.ctr->pslots, (unsigned long long)wnch);
+                    if ((long long)(b + wnch) > p.pcap)
+                        set_err(p.ctr, kDevSlotOverflow);
+                    else
+                        sl = (long long)b;
+                }
+                p.hslot[e] = sl;
+            }
+        }
+    }
+}
+
+// Level 0 of a tile: one entry per source slot (block 0 only).
+template <int W, int MODE>
+__device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
+    constexpr int S = 64 * W;
+    __shared__ int s_scan[S];
+    __shared__ int s_valid;
+    const int t = threadIdx.x;
+    int v = -1, nch = 0;
+    if (t < S) {
+        v = tsrc[t];
+        if (v >= 0) {
+            const long long d = p.off[v + 1] - p.off[v];
+            nch = (int)max(1ll, (d + p.chunk_arcs - 1) / p.chunk_arcs);
+        }
+        s_scan[t] = nch;
+    }
+    if (t == 0) s_valid = 0;
+    __syncthreads();
+    if (t < S && v >= 0) atomicAdd(&s_valid, 1);
+    // inclusive scan over S slots (S <= blockDim.x)
+    for (int o = 1; o < S; o <<= 1) {
+        int y = 0;
+        if (t < S && t >= o) y = s_scan[t - o];
+        __syncthreads();
+        if (t < S) s_scan[t] += y;
+        __syncthreads();
+    }
+    if (t < S && v >= 0) {
+        const int c0 = s_scan[t] - nch;
+        if (c0 + nch > p.ccap || t >= p.hcap) {
+            set_err(p.ctr, kDevChunkOverflow);
+        } else {
+            uint64_t *row = p.vs + (size_t)v * p.vs_stride;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const uint64_t b = (w == (t >> 6)) ? (1ull << (t & 63)) : 0ull;
+                p.hm[(size_t)t * W + w] = b;
+                row[W + w] = b;  // level-0 parity mask
+            }
+            p.hv[t] = v;
+            p.tag[v] = 0;
+            for (int kk = 0; kk < nch; ++kk) p.chunks[c0 + kk] = make_int4(v, kk, nch, t);
+            if (MODE == kModeSpd) {
+                p.sigma[(size_t)v * S + t] = 1.0;
+                long long sl = -1;
+                if (nch > 1) {
+                    const unsigned long long b = atomicAdd(&p.ctr->pslots, (unsigned long long)nch);
+                    if ((long long)(b + nch) > p.pcap)
+                        set_err(p.ctr, kDevSlotOverflow);
+                    else
+                        sl = (long long)b;
+                }
+                p.hslot[t] = sl;
+            }
+        }
+    }
+    if (MODE == kModeSpd) {
+        for (int i = t; i < S * 64; i += blockDim.x) p.qlevel[i] = -1;
+        if (t < W) p.srcflag[t] = 0ull;
+    }
+    __syncthreads();
+    if (t == 0) {
+        p.lev_cnt[0] = (unsigned long long)s_valid;
+        p.lev_ccnt[0] = (unsigned long long)s_scan[S - 1];
+    }
+}
+
+// Expansion of level L (forward pass, Section 2 / Section 4.1).
+template <int W, int MODE>
+__device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
+                              long long cs1, unsigned long long &my_edges, const uint64_t *s_need,
+                              long long gwarp, long long nwarps) {
+    constexpr int S = 64 * W;
+    constexpr int PL = 2 * W;
+    const int lane = threadIdx.x & 31;
+    const int cur = 1 + (L & 1);
+    const int nxt = 1 + ((L + 1) & 1);
+    const int stride = p.vs_stride;
+    const int CH = p.chunk_arcs;
+    for (long long c = gwarp; c < ccnt; c += nwarps) {
+        const int4 ch = p.chunks[cs + c];
+        const int v = ch.x, k = ch.y, e = ch.w;
+        const uint64_t *vrow = p.vs + (size_t)v * stride;
+        uint64_t F[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
+        const long long rb = p.off[v], re = p.off[v + 1];
+        if (k == 0) {
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if (lane == w) p.hm[(size_t)e * W + w] = F[w];
+            if (lane == 0) {
+                uint64_t *vis = p.vs + (size_t)v * stride;
+#pragma unroll
+                for (int w = 0; w < W; ++w) vis[w] |= F[w];
+            }
+            if (MODE == kModeSpd) {
+                if (lane == 0) {
+                    int pc = 0;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
+                    my_edges += (unsigned long long)pc * (unsigned long long)(re - rb);
+                }
+                const uint64_t qm = p.qmask[v];
+#pragma unroll
+                for (int ii = 0; ii < PL; ++ii) {
+                    const int s = lane + 32 * ii;
+                    if (mask_bit<W>(F, s)) {
+                        if (qm) {
+                            uint64_t x = qm & s_need[s];
+                            while (x) {
+                                const int q = __ffsll((long long)x) - 1;
+                                x &= x - 1;
+                                p.qlevel[s * 64 + q] = L;
+                            }
+                        }
+                        if (p.sigma[(size_t)v * S + s] >= 9007199254740992.0)
+                            atomicOr((unsigned long long *)&p.srcflag[s >> 6], 1ull << (s & 63));
+                    }
+                }
+            }
+        }
+        double sig[PL];
+        if (MODE == kModeSpd) {
+#pragma unroll
+            for (int ii = 0; ii < PL; ++ii) {
+                const int s = lane + 32 * ii;
+                sig[ii] = mask_bit<W>(F, s) ? p.sigma[(size_t)v * S + s] : 0.0;
+            }
+        }
+        const long long a0 = rb + (long long)k * CH;
+        const long long a1 = min(re, a0 + CH);
+        for (long long base = a0; base < a1; base += 32) {
+            const long long idx = base + lane;
+            const bool valid = idx < a1;
+            int wv = 0;
+            uint64_t nm[W];
+            bool any = false;
+            if (valid) {
+                wv = p.col[idx];
+                const uint64_t *wrow = p.vs + (size_t)wv * stride;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    nm[w] = F[w] & ~(wrow[w] | wrow[cur * W + w]);
+                    any |= nm[w] != 0ull;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) nm[w] = 0ull;
+            }
+            bool app = false;
+            int wnch = 0;
+            if (any) {
+                uint64_t *wrow = p.vs + (size_t)wv * stride;
+#pragma unroll
+                for (int w = 0; w < W; ++w)
+                    if (nm[w]) atomicOr((unsigned long long *)&wrow[nxt * W + w], (unsigned long long)nm[w]);
+                const int old = atomicMax(&p.tag[wv], L + 1);
+                app = old < L + 1;
+                if (app) {
+                    const long long d = p.off[wv + 1] - p.off[wv];
+                    wnch = (int)max(1ll, (d + CH - 1) / CH);
+                }
+            }
+            warp_append<W, MODE>(p, L, app, wv, wnch, es1, cs1, lane);
+            if (MODE == kModeSpd) {
+                unsigned bal = __ballot_sync(kFull, any);
+                while (bal) {
+                    const int i = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const int wi = __shfl_sync(kFull, wv, i);
+                    uint64_t nmi[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) nmi[w] = __shfl_sync(kFull, nm[w], i);
+                    double *srow = p.sigma + (size_t)wi * S;
+#pragma unroll
+                    for (int ii = 0; ii < PL; ++ii) {
+                        const int s = lane + 32 * ii;
+                        if (mask_bit<W>(nmi, s)) atomicAdd(&srow[s], sig[ii]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// delta for the (v, F) entry once its sum of c over tight out-arcs is known.
+template <int W>
+__device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const uint64_t (&F)[W],
+                                               const double (&acc)[2 * W], const uint64_t *s_need, int lane) {
+    constexpr int S = 64 * W;
+    const uint64_t qm = p.qmask[v];
+    double *row = p.sigma + (size_t)v * S;
+#pragma unroll
+    for (int ii = 0; ii < 2 * W; ++ii) {
+        const int s = lane + 32 * ii;
+        if (mask_bit<W>(F, s)) {
+            const double sv = row[s];
+            const double d = sv * acc[ii];
+            row[s] = (1.0 + d) / sv;
+            if (qm) {
+                uint64_t x = qm & s_need[s];
+                while (x) {
+                    const int q = __ffsll((long long)x) - 1;
+                    x &= x - 1;
+                    p.dep[s * 64 + q] = d;
+                }
+            }
+        }
+    }
+}
+
+// Eq. 4 for the entries of level L (backward pass).
+template <int W>
+__device__ void backward_level(const TravParams &p, int L, long long cs, long long ccnt,
+                               const uint64_t *s_active, const uint64_t *s_need, long long gwarp,
+                               long long nwarps) {
+    constexpr int S = 64 * W;
+    constexpr int PL = 2 * W;
+    constexpr int G = (W >= 4) ? 1 : 4 / W;  // arcs gathered before their adds
+    const int lane = threadIdx.x & 31;
+    const int nx = 1 + ((L + 1) & 1);
+    const int stride = p.vs_stride;
+    const int CH = p.chunk_arcs;
+    for (long long c = gwarp; c < ccnt; c += nwarps) {
+        const int4 ch = p.chunks[cs + c];
+        const int v = ch.x, k = ch.y, nch = ch.z, e = ch.w;
+        uint64_t F[W];
+        bool anyF = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            F[w] = p.hm[(size_t)e * W + w] & s_active[w];
+            anyF |= F[w] != 0ull;
+        }
+        if (!anyF) continue;
+        double acc[PL];
+#pragma unroll
+        for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
+        const long long rb = p.off[v], re = p.off[v + 1];
+        const long long a0 = rb + (long long)k * CH;
+        const long long a1 = min(re, a0 + CH);
+        for (long long base = a0; base < a1; base += 32) {
+            const long long idx = base + lane;
+            int wv = 0;
+            uint64_t tm[W];
+            bool any = false;
+            if (idx < a1) {
+                wv = p.col[idx];
+                const uint64_t *wrow = p.vs + (size_t)wv * stride;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    tm[w] = F[w] & wrow[nx * W + w];
+                    any |= tm[w] != 0ull;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) tm[w] = 0ull;
+            }
+            unsigned bal = __ballot_sync(kFull, any);
+            while (bal) {
+                double val[G][PL];
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi) {
+                    int i = -1;
+                    if (bal) {
+                        i = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                    }
+                    const int src_lane = i < 0 ? 0 : i;
+                    const int wi = __shfl_sync(kFull, wv, src_lane);
+                    uint64_t tmi[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) tmi[w] = __shfl_sync(kFull, tm[w], src_lane);
+                    const double *crow = p.sigma + (size_t)wi * S;
+#pragma unroll
+                    for (int ii = 0; ii < PL; ++ii) {
+                        const int s = lane + 32 * ii;
+                        val[gi][ii] = (i >= 0 && mask_bit<W>(tmi, s)) ? crow[s] : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int gi = 0; gi < G; ++gi)
+#pragma unroll
+                    for (int ii = 0; ii < PL; ++ii) acc[ii] += val[gi][ii];
+            }
+        }
+        if (nch == 1) {
+            finalize_entry<W>(p, v, F, acc, s_need, lane);
+        } else {
+            const long long slot0 = p.hslot[e];
+            double *prow = p.partial + (size_t)(slot0 + k) * S;
+#pragma unroll
+            for (int ii = 0; ii < PL; ++ii) __stcg(&prow[lane + 32 * ii], acc[ii]);
+            __threadfence();
+            int prev = 0;
+            if (lane == 0) prev = atomicAdd(&p.pdone[slot0], 1);
+            prev = __shfl_sync(kFull, prev, 0);
+            if (prev == nch - 1) {
+                __threadfence();
+#pragma unroll
+                for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
+                for (int kk = 0; kk < nch; ++kk) {
+                    const double *q = p.partial + (size_t)(slot0 + kk) * S;
+#pragma unroll
+                    for (int ii = 0; ii < PL; ++ii) acc[ii] += __ldcg(&q[lane + 32 * ii]);
+                }
+                if (lane == 0) p.pdone[slot0] = 0;
+                finalize_entry<W>(p, v, F, acc, s_need, lane);
+            }
+        }
+    }
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
+    constexpr int S = 64 * W;
+    const int lane = threadIdx.x & 31;
+    const long long wpb = blockDim.x >> 5;
+    const long long gwarp = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+    const long long nwarps = (long long)gridDim.x * wpb;
+    const long long gthr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    uint32_t gen = 0;
+    __shared__ uint64_t s_need[S];
+    __shared__ int32_t s_minql[S];
+    __shared__ uint64_t s_active[W];
+    __shared__ int32_t s_lstop;
+    unsigned long long my_edges = 0;
+
+    for (long long tile = 0; tile < p.ntiles; ++tile) {
+        const int32_t *tsrc = p.srcs + tile * S;
+        if (blockIdx.x == 0) init_tile<W, MODE>(p, tsrc);
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
+            const int32_t v = tsrc[s];
+            s_need[s] = (MODE == kModeSpd && v >= 0) ? p.need[v] : 0ull;
+        }
+        if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+
+        // ---------------- forward ----------------
+        long long es = 0, cs = 0, es_prev = 0;
+        int L = 0;
+        long long total = 0;
+        for (;;) {
+            const long long ecnt = (long long)ld_vol(&p.lev_cnt[L]);
+            const long long ccnt = (long long)ld_vol(&p.lev_ccnt[L]);
+            const long long es1 = es + ecnt, cs1 = cs + ccnt;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                p.lev_start[L] = es;
+                p.lev_cstart[L] = cs;
+                p.lev_start[L + 1] = es1;
+                p.lev_cstart[L + 1] = cs1;
+            }
+            if (L >= 1) {
+                const int nxt = 1 + ((L + 1) & 1);
+                for (long long e = es_prev + gthr; e < es; e += nthr) {
+                    const int v = p.hv[e];
+                    uint64_t *row = p.vs + (size_t)v * p.vs_stride;
+#pragma unroll
+                    for (int w = 0; w < W; ++w)
+                        atomicAnd((unsigned long long *)&row[nxt * W + w], ~(unsigned long long)p.hm[e * W + w]);
+                }
+            }
+            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, my_edges, s_need, gwarp, nwarps);
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+            total = es1;
+            if (ld_vol(&p.lev_cnt[L + 1]) == 0ull) break;
+            if (L + 2 > p.maxlev) {
+                if (threadIdx.x == 0) set_err(p.ctr, kDevLevelOverflow);
+                return;
+            }
+            es_prev = es;
+            es = es1;
+            cs = cs1;
+            ++L;
+        }
+        const int Lmax = L;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&p.ctr->levels_max, (unsigned long long)Lmax);
+
+        // ---------------- backward ----------------
+        if (MODE == kModeSpd && !(p.flags & kFlagNoBackward)) {
+            if (threadIdx.x == 0) s_lstop = 0x7fffffff;
+            __syncthreads();
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                int mq = 0x7fffffff;
+                if (tsrc[s] >= 0) {
+                    if (p.flags & kFlagFullBackward) {
+                        mq = 0;
+                    } else {
+                        uint64_t x = s_need[s];
+                        while (x) {
+                            const int q = __ffsll((long long)x) - 1;
+                            x &= x - 1;
+                            const int lv = p.qlevel[s * 64 + q];
+                            if (lv >= 0 && lv < mq) mq = lv;
+                        }
+                    }
+                }
+                s_minql[s] = mq;
+                atomicMin(&s_lstop, mq);
+            }
+            __syncthreads();
+            const int lstop = s_lstop;
+            for (int Lb = Lmax; Lb >= lstop && lstop <= Lmax; --Lb) {
+                if (threadIdx.x < W) {
+                    uint64_t a = 0;
+                    for (int b = 0; b < 64; ++b)
+                        if (s_minql[threadIdx.x * 64 + b] <= Lb) a |= 1ull << b;
+                    s_active[threadIdx.x] = a;
+                }
+                __syncthreads();
+                const int cur = 1 + (Lb & 1);
+                if (Lb + 2 <= Lmax) {
+                    const long long e0 = p.lev_start[Lb + 2], e1 = e0 + (long long)p.lev_cnt[Lb + 2];
+                    for (long long e = e0 + gthr; e < e1; e += nthr) {
+                        uint64_t *row = p.vs + (size_t)p.hv[e] * p.vs_stride;
+#pragma unroll
+                        for (int w = 0; w < W; ++w)
+                            atomicAnd((unsigned long long *)&row[cur * W + w], ~(unsigned long long)p.hm[e * W + w]);
+                    }
+                }
+                {
+                    const long long e0 = p.lev_start[Lb], e1 = e0 + (long long)p.lev_cnt[Lb];
+                    for (long long e = e0 + gthr; e < e1; e += nthr) {
+                        uint64_t *row = p.vs + (size_t)p.hv[e] * p.vs_stride;
+#pragma unroll
+                        for (int w = 0; w < W; ++w)
+                            atomicOr((unsigned long long *)&row[cur * W + w], (unsigned long long)p.hm[e * W + w]);
+                    }
+                }
+                backward_level<W>(p, Lb, p.lev_cstart[Lb], (long long)p.lev_ccnt[Lb], s_active, s_need, gwarp,
+                                  nwarps);
+                if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+            }
+        }
+
+        // ---------------- tile end ----------------
+        if (MODE == kModeSpd && blockIdx.x == 0 && threadIdx.x < 64) {
+            const int q = threadIdx.x;
+            const bool exact = (p.exact_q >> q) & 1ull;
+            double sum = 0.0;
+            bool flagged = false;
+            for (int s = 0; s < S; ++s) {
+                if (tsrc[s] < 0) continue;
+                double mlt = 0.0;
+                if (exact) {
+                    mlt = ((s_need[s] >> q) & 1ull) ? 1.0 : 0.0;
+                } else if (p.mult) {
+                    mlt = (double)p.mult[((size_t)tile * S + s) * 64 + q];
+                }
+                if (mlt != 0.0) {
+                    sum += mlt * p.dep[s * 64 + q];
+                    if ((p.srcflag[s >> 6] >> (s & 63)) & 1ull) flagged = true;
+                }
+            }
+            p.tile_partial[tile * 64 + q] = sum;
+            if (flagged) p.qflags[q] |= 1u;
+        }
+        if (MODE == kModeReach) {
+            for (long long e = gthr; e < total; e += nthr)
+                atomicOr((unsigned long long *)&p.rvmask[p.hv[e]], (unsigned long long)p.hm[e * W]);
+        }
+        if (!(p.flags & kFlagNoReset)) {
+            for (long long e = gwarp; e < total; e += nwarps) {
+                const int v = p.hv[e];
+                if (MODE == kModeSpd) {
+                    uint64_t F[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) F[w] = p.hm[e * W + w];
+                    double *row = p.sigma + (size_t)v * S;
+#pragma unroll
+                    for (int ii = 0; ii < 2 * W; ++ii) {
+                        const int s = lane + 32 * ii;
+                        if (mask_bit<W>(F, s)) row[s] = 0.0;
+                    }
+                }
+                if (lane < p.vs_stride) p.vs[(size_t)v * p.vs_stride + lane] = 0ull;
+                if (lane == 0) p.tag[v] = -1;
+            }
+            if (blockIdx.x == 0) {
+                for (int l = threadIdx.x; l <= Lmax + 1; l += blockDim.x) {
+                    p.lev_cnt[l] = 0ull;
+                    p.lev_ccnt[l] = 0ull;
+                }
+                if (threadIdx.x == 0) p.ctr->pslots = 0ull;
+            }
+        }
+        if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+    }
+    // fold per-thread edge counts
+    if (MODE == kModeSpd && my_edges) atomicAdd(&p.ctr->edges, my_edges);
+}
+
+template <int W, int MODE>
+bc_status launch(bc_graph *g, TravParams &p) {
+    auto kern = trav_kernel<W, MODE>;
+    int threads = g->block_threads;
+    int per_sm = 0;
+    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    if (per_sm < 1) return set_error(BC_E_INTERNAL, "traversal kernel cannot be resident");
+    dim3 grid((unsigned)(g->num_sms * per_sm)), block((unsigned)threads);
+    void *args[] = {(void *)&p};
+    BCD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, grid, block, args, 0, g->stream));
+    g->launches += 1;
+    return BC_OK;
+}
+
+}  // namespace
+
+bc_status reset_dense_state(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    BCD_CUDA(cudaMemsetAsync(ws.vs, 0, sizeof(uint64_t) * (size_t)ws.n * ws.vs_stride, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.tag, 0xff, sizeof(int32_t) * (size_t)ws.n, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.sigma, 0, sizeof(double) * (size_t)ws.n * 64 * ws.W, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)ws.pcap, g->stream));
+    return BC_OK;
+}
+
+bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out) {
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        bcd_workspace &ws = g->ws;
+        p.vs = ws.vs;
+        p.vs_stride = ws.vs_stride;
+        p.tag = ws.tag;
+        p.sigma = ws.sigma;
+        p.hv = ws.hv;
+        p.hm = ws.hm;
+        p.hslot = ws.hslot;
+        p.hcap = ws.hcap;
+        p.chunks = ws.chunks;
+        p.ccap = ws.ccap;
+        p.partial = ws.partial;
+        p.pdone = ws.pdone;
+        p.pcap = ws.pcap;
+        p.lev_cnt = ws.lev_cnt;
+        p.lev_ccnt = ws.lev_ccnt;
+        p.lev_start = ws.lev_start;
+        p.lev_cstart = ws.lev_cstart;
+        p.maxlev = ws.maxlev;
+        p.ctr = ws.ctr;
+        p.n = g->n;
+        p.chunk_arcs = g->chunk_arcs;
+        p.timeout_ns = 10.0e9;
+        BCD_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), g->stream));
+        bc_status st = BC_E_INTERNAL;
+        if (p.mode == kModeReach) {
+            if (W != 1) return set_error(BC_E_INTERNAL, "reach traversal runs with one mask word");
+            st = launch<1, kModeReach>(g, p);
+        } else if (W == 1) {
+            st = launch<1, kModeSpd>(g, p);
+        } else if (W == 2) {
+            st = launch<2, kModeSpd>(g, p);
+        } else if (W == 4) {
+            st = launch<4, kModeSpd>(g, p);
+        } else {
+            return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
+        }
+        if (st != BC_OK) return st;
+        Counters c;
+        BCD_CUDA(cudaMemcpyAsync(&c, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->stream));
+        BCD_CUDA(cudaStreamSynchronize(g->stream));
+        if (c.err == kDevOk) {
+            if (levels_out) *levels_out = (int)c.levels_max;
+            if (edges_out) *edges_out = c.edges;
+            return BC_OK;
+        }
+        if (c.err == kDevTimeout) {
+            reset_dense_state(g);
+            return set_error(BC_E_TIMEOUT, "traversal: a grid barrier wait timed out");
+        }
+        if (c.err == kDevLevelOverflow) {
+            reset_dense_state(g);
+            return set_error(BC_E_INTERNAL, "traversal: level count exceeded the vertex count");
+        }
+        // capacity overflow: grow the level history and retry from a clean state
+        BCD_TRY(grow_history(g));
+        BCD_TRY(reset_dense_state(g));
+        if (p.mode == kModeReach && p.rvmask)
+            BCD_CUDA(cudaMemsetAsync(p.rvmask, 0, sizeof(uint64_t) * (size_t)g->n, g->stream));
+        if (p.qflags) BCD_CUDA(cudaMemsetAsync(p.qflags, 0, sizeof(uint32_t) * 64, g->stream));
+    }
+    return set_error(BC_E_OOM, "traversal: level history did not fit after growing it");
+}
+
+}  // namespace bcd

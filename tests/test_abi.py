@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every function include/bcd.h
+declares; the binding's signature table covers the same set. No GPU needed:
+nothing here calls into device code."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "bcd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(bc_[A-Za-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1708_08739_gb300 import build
+    build.build()
+    import paper_1708_08739_gb300 as bcd
+    return bcd
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ["bc_graph_create", "bc_graph_destroy", "bc_rv_compute", "bc_exact", "bc_approx", "bc_approx_T",
+              "bc_batch", "bc_draw_samples", "bc_spd_probe", "bc_last_error"]:
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    import ctypes
+    L = ctypes.CDLL(built_lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert set(built_lib._SIGNATURES) == declared_functions()
+
+
+def test_binding_loads_and_reports_version(built_lib):
+    assert "sm_103a" in built_lib.bc_version()
+    assert built_lib.bc_last_error() == ""
+    assert built_lib.bc_samples_for(0.01, 0.1) == 14979
+    assert built_lib.bc_samples_for(0.02, 0.1) == 3745
+    with pytest.raises(built_lib.BCError):
+        built_lib.bc_samples_for(0.0, 0.1)
+
+
+def test_no_oracle_in_product_path():
+    """The CUDA library and its binding never reference the oracle."""
+    pkg = os.path.join(ROOT, "paper_1708_08739_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "bc_oracle" not in src and "liboracle" not in src, f

@@ -1,0 +1,293 @@
+"""CUDA library against the CPU oracle, element by element, on seeded inputs.
+
+Bars: RV lists, distances, sigma and sampled source lists bit-exact; delta
+and BC within a relative 1e-9 (fp64 sums in a different order). Sizes span
+several tiles and ragged tails; edge cases cover empty and trivial inputs,
+long level chains, heavy rows split into many chunks and sigma past 2^53.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+from helpers import csr
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+UNREACHED = np.iinfo(np.uint64).max
+
+
+@pytest.fixture(scope="module")
+def bcd():
+    import paper_1708_08739_gb300 as m
+    m.lib()
+    return m
+
+
+def close(a, b, rel=REL):
+    return abs(a - b) <= rel * max(1.0, abs(b))
+
+
+def make(bcd, g, **cfg):
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    if cfg:
+        bcd.bc_set_config(dg, **cfg)
+    return dg
+
+
+@pytest.fixture(scope="module")
+def er1():
+    """Directed ER, 2,000 vertices, 16,000 arcs, seed 1."""
+    g = gg.erdos_renyi(2000, 16000, 1)
+    return g, O.Graph.from_csr(g)
+
+
+@pytest.fixture(scope="module")
+def sparse_er():
+    """Sparser ER with many small reach sets and long BFS depth."""
+    g = gg.erdos_renyi(3000, 3600, 2)
+    return g, O.Graph.from_csr(g)
+
+
+def test_reverse_graph(bcd, er1):
+    g, og = er1
+    dg = make(bcd, g)
+    roff, rcol, _ = bcd.bc_graph_reverse(dg)
+    assert np.array_equal(roff, og.roff)
+    for v in range(g.n):  # row order is unspecified: compare sets
+        assert np.array_equal(np.sort(rcol[roff[v]:roff[v + 1]]), og.rcol[og.roff[v]:og.roff[v + 1]])
+
+
+@pytest.mark.parametrize("which", ["er1", "sparse_er"])
+def test_rv_lists_bit_exact(bcd, which, request):
+    g, og = request.getfixturevalue(which)
+    dg = make(bcd, g)
+    for r in list(gg.random_vertices(g.n, 24, 102)) + [0, g.n - 1]:
+        assert np.array_equal(bcd.bc_rv_compute(dg, int(r)), O.rv(og, int(r))), r
+
+
+@pytest.mark.parametrize("tile_words", [1, 2, 4])
+def test_probe_dist_sigma_delta(bcd, er1, tile_words):
+    g, og = er1
+    dg = make(bcd, g, tile_words=tile_words)
+    srcs = np.array(sorted(set(gg.random_vertices(g.n, 40, 7).tolist())), dtype=np.int32)[:37]
+    tgts = gg.random_vertices(g.n, 20, 8)
+    tgts = np.array([t for t in dict.fromkeys(tgts.tolist())], dtype=np.int32)
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, tgts)
+    for i, s in enumerate(srcs.tolist()):
+        st = O.source_state(og, s)
+        assert np.array_equal(dist[i], st["dist"]), s
+        assert np.array_equal(sig[i], st["sigma"]), s
+        assert flags[i] == 0
+        for j, t in enumerate(tgts.tolist()):
+            if t == s:
+                continue
+            assert close(dep[i, j], st["delta"][t]), (s, t, dep[i, j], st["delta"][t])
+
+
+@pytest.mark.parametrize("cfg", [{}, {"tile_words": 2}, {"tile_words": 4}, {"chunk_arcs": 32},
+                                 {"block_threads": 256, "chunk_arcs": 64}])
+def test_exact_matches_oracle(bcd, er1, cfg):
+    g, og = er1
+    dg = make(bcd, g, **cfg)
+    qs = gg.random_vertices(g.n, 16, 102)
+    for r in qs.tolist():
+        got, info = bcd.bc_exact(dg, r)
+        want, k, f = O.bc_exact(og, r, 0)
+        assert info["rv_size"] == k
+        assert close(got, want), (r, got, want)
+        assert info["flags"] == f
+
+
+def test_exact_matches_all_sources_brandes(bcd):
+    g = gg.erdos_renyi(400, 2400, 77)
+    og = O.Graph.from_csr(g)
+    allbc = O.bc_all(og)
+    dg = make(bcd, g)
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in range(g.n)])
+    for r in range(g.n):
+        assert out[r]["status"] == 0
+        assert close(out[r]["bc"], allbc[r]), (r, out[r]["bc"], allbc[r])
+
+
+def test_batch_equals_single(bcd, sparse_er):
+    g, og = sparse_er
+    dg = make(bcd, g)
+    qs = gg.random_vertices(g.n, 100, 5).tolist()  # > 64: two groups, repeated roots possible
+    out, info = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    for r, o in zip(qs, out):
+        single, _ = bcd.bc_exact(dg, r)
+        want, k, _ = O.bc_exact(og, r, 0)
+        assert o["status"] == 0 and o["rv_size"] == k
+        assert close(o["bc"], want) and close(single, want)
+    assert info["queries"] == 100
+
+
+def test_sampled_draws_and_estimate(bcd, er1):
+    g, og = er1
+    dg = make(bcd, g)
+    for r, T, seed in [(5, 1000, 7), (1234, 333, 99), (77, 14979, 7)]:
+        draws, k = bcd.bc_draw_samples(dg, r, T, seed)
+        want, wdraws, wk, _ = O.bc_approx(og, r, T, seed, 0)
+        assert k == wk
+        assert np.array_equal(draws, wdraws)
+        got, info = bcd.bc_approx_T(dg, r, T, seed)
+        assert info["samples"] == T and info["rv_size"] == k
+        assert close(got, want), (r, got, want)
+
+
+def test_approx_eps_delta(bcd, er1):
+    g, og = er1
+    dg = make(bcd, g)
+    T = O.samples_for(0.05, 0.1)
+    got, info = bcd.bc_approx(dg, 9, 0.05, 0.1, 7)
+    want, _, _, _ = O.bc_approx(og, 9, T, 7, 0)
+    assert info["samples"] == T
+    assert close(got, want)
+
+
+def test_mixed_batch(bcd, er1):
+    """Exact, sampled and hybrid queries in one group, repeated roots."""
+    g, og = er1
+    dg = make(bcd, g)
+    specs = []
+    rs = gg.random_vertices(g.n, 30, 31).tolist()
+    for i, r in enumerate(rs):
+        kind = i % 4
+        if kind == 0:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_EXACT})
+        elif kind == 1:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 700, "seed": 7})
+        elif kind == 2:
+            specs.append({"r": rs[0], "kind": bcd.BC_QUERY_APPROX_T, "T": 500, "seed": i})
+        else:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_HYBRID, "T": 1000, "seed": 3})
+    out, _ = bcd.bc_batch(dg, specs)
+    for s, o in zip(specs, out):
+        assert o["status"] == 0
+        r = s["r"]
+        rvk = O.rv(og, r).shape[0]
+        if s["kind"] == bcd.BC_QUERY_EXACT or (s["kind"] == bcd.BC_QUERY_HYBRID and rvk <= s["T"]):
+            want = O.bc_exact(og, r, 0)[0]
+            assert o["samples"] == 0
+        else:
+            want = O.bc_approx(og, r, s["T"], s["seed"], 0)[0]
+            assert o["samples"] == (s["T"] if rvk > 0 and g.out_degree()[r] > 0 else 0)
+        assert close(o["bc"], want), (s, o["bc"], want)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_trivial_zero_and_empty_rv(bcd):
+    g = csr(5, [(0, 1), (1, 2), (3, 2), (2, 4)])
+    dg = make(bcd, g)
+    bc, info = bcd.bc_exact(dg, 4)  # out-degree 0
+    assert bc == 0.0 and info["flags"] & bcd.BC_FLAG_TRIVIAL_ZERO and info["rv_size"] == 0
+    bc, info = bcd.bc_exact(dg, 0)  # in-degree 0: RV empty
+    assert bc == 0.0 and info["rv_size"] == 0 and info["sources_run"] == 0
+    bc, info = bcd.bc_exact(dg, 2)
+    assert bc == 3.0 and info["rv_size"] == 3  # pairs (0,4),(1,4),(3,4)
+    bc, info = bcd.bc_approx_T(dg, 0, 10, 1)
+    assert bc == 0.0 and info["samples"] == 0
+    assert bcd.bc_rv_compute(dg, 0).shape[0] == 0
+    draws, k = bcd.bc_draw_samples(dg, 4, 10, 1)
+    assert k == 0 and draws.shape[0] == 0
+
+
+def test_graph_without_arcs_and_single_vertex(bcd):
+    g = gg.CSR(1, np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    dg = make(bcd, g)
+    assert bcd.bc_exact(dg, 0)[0] == 0.0
+    g = gg.CSR(7, np.zeros(8, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    dg = make(bcd, g)
+    assert bcd.bc_exact(dg, 3)[0] == 0.0
+    assert bcd.bc_rv_compute(dg, 3).shape[0] == 0
+
+
+def test_long_path_levels(bcd):
+    n = 3000  # 2999 BFS levels in one tile
+    g = csr(n, [(i, i + 1) for i in range(n - 1)])
+    dg = make(bcd, g)
+    for r in [1, 1500, n - 2]:
+        assert bcd.bc_exact(dg, r)[0] == r * (n - 1 - r)
+
+
+def test_heavy_rows_chunked(bcd):
+    """A hub with 20,000 out-arcs and 20,000 in-arcs: rows split into many
+    chunks whose partial sums are combined in order."""
+    n = 20001
+    arcs = [(0, i) for i in range(1, n)] + [(i, 0) for i in range(1, n)]
+    arcs += [(i, i + 1) for i in range(1, n - 1)]
+    g = csr(n, arcs)
+    og = O.Graph.from_csr(g)
+    want = {r: O.bc_exact(og, r, 0)[0] for r in [0, 5, 19999]}
+    for cfg in [{}, {"chunk_arcs": 32}]:
+        dg = make(bcd, g, **cfg)
+        for r in want:
+            got = bcd.bc_exact(dg, r)[0]
+            assert close(got, want[r]), (cfg, r, got, want[r])
+
+
+@pytest.mark.parametrize("k", [52, 53, 54, 60])
+def test_sigma_flag(bcd, k):
+    arcs = []
+    for i in range(k):
+        a, b, c, d = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        arcs += [(a, b), (a, c), (b, d), (c, d)]
+    arcs.append((3 * k, 3 * k + 1))
+    g = csr(3 * k + 2, arcs)
+    og = O.Graph.from_csr(g)
+    dg = make(bcd, g)
+    dist, sig, _, flags = bcd.bc_spd_probe(dg, [0], [3 * k])
+    st = O.source_state(og, 0)
+    assert int(dist[0, 3 * k]) == 2 * k
+    if k <= 52:
+        assert np.array_equal(sig[0], st["sigma"])
+    assert bool(flags[0] & bcd.BC_FLAG_SIGMA_2_53) == bool(st["flags"] & O.FLAG_SIGMA_GT_2_53)
+    bc, info = bcd.bc_exact(dg, 3 * k)  # r = sink of the chain: 2^k paths from 0 reach it
+    want, _, wf = O.bc_exact(og, 3 * k, 0)
+    assert bool(info["flags"] & bcd.BC_FLAG_SIGMA_2_53) == bool(wf & O.FLAG_SIGMA_GT_2_53)
+    if k <= 52:
+        assert close(bc, want)
+
+
+def test_invalid_graphs_rejected(bcd):
+    def create(n, off, cols, w=None):
+        return bcd.bc_graph_create(n, np.array(off, dtype=np.int64), np.array(cols, dtype=np.int32),
+                                   None if w is None else np.array(w, dtype=np.uint32))
+    with pytest.raises(bcd.BCError) as e:
+        create(3, [0, 1, 1, 1], [0])  # self-loop
+    assert e.value.status == bcd.BC_E_INVALID_GRAPH
+    with pytest.raises(bcd.BCError) as e:
+        create(3, [0, 2, 2, 2], [2, 1])  # unsorted row
+    assert e.value.status == bcd.BC_E_INVALID_GRAPH
+    with pytest.raises(bcd.BCError) as e:
+        create(3, [0, 2, 2, 2], [1, 1])  # repeated arc
+    assert e.value.status == bcd.BC_E_INVALID_GRAPH
+    with pytest.raises(bcd.BCError) as e:
+        create(3, [0, 1, 1, 1], [5])  # head out of range
+    assert e.value.status == bcd.BC_E_INVALID_ARG
+    with pytest.raises(bcd.BCError) as e:
+        create(3, [0, 2, 1, 1], [1, 2])  # offsets decrease
+    assert e.value.status == bcd.BC_E_INVALID_ARG
+    dg = create(3, [0, 1, 2, 2], [1, 2])
+    with pytest.raises(bcd.BCError) as e:
+        bcd.bc_exact(dg, 3)
+    assert e.value.status == bcd.BC_E_INVALID_ARG
+    with pytest.raises(bcd.BCError):
+        bcd.bc_approx(dg, 1, 0.0, 0.1, 1)
+    out, _ = bcd.bc_batch(dg, [{"r": 1}, {"r": -1}, {"r": 1, "kind": bcd.BC_QUERY_APPROX, "eps": 0.1,
+                                                     "delta": 2.0}])
+    assert out[0]["status"] == 0 and out[0]["bc"] == 1.0
+    assert out[1]["status"] == bcd.BC_E_INVALID_ARG and out[2]["status"] == bcd.BC_E_INVALID_ARG
+
+
+def test_device_input_arrays(bcd, er1):
+    torch = pytest.importorskip("torch")
+    g, og = er1
+    off = torch.from_numpy(g.offsets).cuda()
+    col = torch.from_numpy(g.cols).cuda()
+    dg = bcd.bc_graph_create(g.n, off, col)
+    r = 11
+    assert close(bcd.bc_exact(dg, r)[0], O.bc_exact(og, r, 0)[0])
