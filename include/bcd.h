@@ -190,6 +190,11 @@ typedef struct {
     int64_t edges_traversed;  /* sum over those sources of |E_s| */
     int64_t launches;         /* kernel launches issued */
     double ms_rv, ms_sample, ms_spd, ms_total;
+    double ms_forward;        /* wall time of the traversal kernel's forward */
+    double ms_backward;       /* ... and backward passes (one block's view) */
+    int64_t tiles;            /* tiles of 64*tile_words sources run */
+    int32_t max_level;        /* deepest SPD level met */
+    int32_t grid_blocks;      /* blocks of the persistent traversal launch */
 } bc_batch_info;
 
 /*

@@ -64,7 +64,9 @@ class bc_result(C.Structure):
 class bc_batch_info(C.Structure):
     _fields_ = [("queries", C.c_int64), ("sources_run", C.c_int64), ("edges_traversed", C.c_int64),
                 ("launches", C.c_int64), ("ms_rv", C.c_double), ("ms_sample", C.c_double),
-                ("ms_spd", C.c_double), ("ms_total", C.c_double)]
+                ("ms_spd", C.c_double), ("ms_total", C.c_double), ("ms_forward", C.c_double),
+                ("ms_backward", C.c_double), ("tiles", C.c_int64), ("max_level", C.c_int32),
+                ("grid_blocks", C.c_int32)]
 
 
 class bc_config(C.Structure):

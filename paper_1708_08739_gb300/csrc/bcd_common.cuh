@@ -33,7 +33,21 @@ struct Counters {
     unsigned long long edges;      // sum over reached (v, s) of out-degree(v)
     unsigned long long pslots;     // partial-row slots handed out this tile
     unsigned long long levels_max; // deepest level met over all tiles
-    unsigned long long pad1;
+    unsigned long long ns_fwd;     // block 0's wall time in forward passes
+    unsigned long long ns_bwd;     // ... in backward passes
+    unsigned long long ns_other;   // ... in tile set-up and tear-down
+};
+
+// One unit of expansion work: arcs [a0, a0 + na) of vertex v, the k-th of
+// nch chunks of history entry e.
+struct __align__(16) Chunk {
+    int32_t v;
+    int32_t e;
+    int32_t k;
+    int32_t nch;
+    int64_t a0;
+    int32_t na;
+    int32_t pad;
 };
 
 // Traversal modes of the persistent kernel.
@@ -67,7 +81,7 @@ struct TravParams {
     uint64_t *hm;       // [hcap * W]
     int64_t *hslot;     // [hcap]
     int64_t hcap;
-    int4 *chunks;       // [ccap] {v, k, nch, e}
+    Chunk *chunks;      // [ccap]
     int64_t ccap;
     double *partial;    // [pcap * S]
     int32_t *pdone;     // [pcap]
@@ -117,7 +131,7 @@ struct bcd_workspace {
     uint64_t *hm = nullptr;
     int64_t *hslot = nullptr;
     int64_t hcap = 0;
-    int4 *chunks = nullptr;
+    bcd::Chunk *chunks = nullptr;
     int64_t ccap = 0;
     double *partial = nullptr;
     int32_t *pdone = nullptr;
@@ -185,6 +199,10 @@ struct bc_graph {
     int block_threads = 512;
     bcd_workspace ws;
     int64_t launches = 0;
+    int last_grid = 0;                       // blocks of the last traversal launch
+    unsigned long long last_ns_fwd = 0;      // phase times of the last traversal launch
+    unsigned long long last_ns_bwd = 0;
+    unsigned long long last_ns_other = 0;
 };
 
 namespace bcd {

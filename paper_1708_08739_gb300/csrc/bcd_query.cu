@@ -294,7 +294,9 @@ struct GQuery {
 
 struct GroupTimes {
     float rv = 0, sample = 0, spd = 0, total = 0;
+    double fwd = 0, bwd = 0;
     int64_t sources = 0;
+    int64_t tiles = 0;
     unsigned long long edges = 0;
     int levels = 0;
 };
@@ -518,6 +520,8 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         p.qflags = ws.qflags;
         p.srcflag = ws.srcflag;
         BCD_TRY(run_traversal(g, W, p, &levels, &edges));
+        tm.fwd = g->last_ns_fwd * 1e-6;
+        tm.bwd = g->last_ns_bwd * 1e-6;
         std::vector<double> scale(64, 1.0);
         for (int i = 0; i < nq; ++i)
             if (qs[i].sampled && qs[i].rv > 0) scale[i] = (double)qs[i].rv / (double)qs[i].T;
@@ -547,6 +551,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     tm.spd = ev.ms(2, 3);
     tm.total = ev.ms(0, 3);
     tm.sources = nd;
+    tm.tiles = ntiles;
     tm.edges = edges;
     tm.levels = levels;
     return BC_OK;
@@ -583,6 +588,11 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.ms_sample += t.sample;
         bi.ms_spd += t.spd;
         bi.ms_total += t.total;
+        bi.ms_forward += t.fwd;
+        bi.ms_backward += t.bwd;
+        bi.tiles += t.tiles;
+        bi.max_level = std::max(bi.max_level, (int32_t)t.levels);
+        bi.grid_blocks = g->last_grid;
         group.clear();
         return BC_OK;
     };
@@ -680,6 +690,7 @@ static bc_status single(bc_graph *g, const bc_query &q, double *bc, bc_info *inf
         info->samples = r.samples;
         info->sources_run = bi.sources_run;
         info->edges_traversed = bi.edges_traversed;
+        info->max_level = bi.max_level;
         info->flags = r.flags;
         info->ms_rv = bi.ms_rv;
         info->ms_sample = bi.ms_sample;

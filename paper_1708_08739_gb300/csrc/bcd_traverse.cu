@@ -94,11 +94,55 @@ __device__ __forceinline__ bool mask_bit(const uint64_t (&m)[W], int s) {
     return (m[s >> 6] >> (s & 63)) & 1ull;
 }
 
+// Bytes of shared memory each warp stages backward gathers in.
+constexpr int kStageBytes = 4096;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ Chunk load_chunk(const Chunk *c) {
+    const int4 a = reinterpret_cast<const int4 *>(c)[0];
+    const int4 b = reinterpret_cast<const int4 *>(c)[1];
+    Chunk r;
+    r.v = a.x;
+    r.e = a.y;
+    r.k = a.z;
+    r.nch = a.w;
+    r.a0 = (int64_t)(((unsigned long long)(unsigned)b.y << 32) | (unsigned)b.x);
+    r.na = b.z;
+    r.pad = 0;
+    return r;
+}
+
+__device__ __forceinline__ void store_chunk(Chunk *c, int v, int e, int k, int nch, long long a0, int na) {
+    int4 *d = reinterpret_cast<int4 *>(c);
+    d[0] = make_int4(v, e, k, nch);
+    d[1] = make_int4((int)(unsigned)(a0 & 0xffffffffll), (int)(unsigned)((unsigned long long)a0 >> 32), na, 0);
+}
+
+// Writes the chunk descriptors of a vertex with arcs [rb, re).
+__device__ __forceinline__ void emit_chunks(const TravParams &p, long long c0, int v, int e, int nch, long long rb,
+                                            long long re) {
+    const int CH = p.chunk_arcs;
+    for (int kk = 0; kk < nch; ++kk) {
+        const long long a0 = rb + (long long)kk * CH;
+        const long long a1 = min(re, a0 + CH);
+        store_chunk(&p.chunks[c0 + kk], v, e, kk, nch, a0, (int)max(0ll, a1 - a0));
+    }
+}
+
 // Appends the vertices a warp discovered at level L+1 (one entry and nch
 // chunks each), with one pair of counter atomics per warp.
 template <int W, int MODE>
-__device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app, int wv, int wnch,
-                                            long long es1, long long cs1, int lane) {
+__device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app, int wv, int wnch, long long wrb,
+                                            long long wre, long long es1, long long cs1, int lane) {
     const unsigned am = __ballot_sync(kFull, app);
     if (am == 0) return;
     const int rank = __popc(am & ((1u << lane) - 1u));
@@ -126,7 +170,7 @@ __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app
             set_err(p.ctr, kDevChunkOverflow);
         } else {
             p.hv[e] = wv;
-            for (int kk = 0; kk < wnch; ++kk) p.chunks[c0 + kk] = make_int4(wv, kk, wnch, (int)e);
+            emit_chunks(p, c0, wv, (int)e, wnch, wrb, wre);
             if (MODE == kModeSpd) {
                 long long sl = -1;
                 if (wnch > 1) {
@@ -150,18 +194,19 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
     __shared__ int s_valid;
     const int t = threadIdx.x;
     int v = -1, nch = 0;
+    long long rb = 0, re = 0;
     if (t < S) {
         v = tsrc[t];
         if (v >= 0) {
-            const long long d = p.off[v + 1] - p.off[v];
-            nch = (int)max(1ll, (d + p.chunk_arcs - 1) / p.chunk_arcs);
+            rb = p.off[v];
+            re = p.off[v + 1];
+            nch = (int)max(1ll, (re - rb + p.chunk_arcs - 1) / p.chunk_arcs);
         }
         s_scan[t] = nch;
     }
     if (t == 0) s_valid = 0;
     __syncthreads();
     if (t < S && v >= 0) atomicAdd(&s_valid, 1);
-    // inclusive scan over S slots (S <= blockDim.x)
     for (int o = 1; o < S; o <<= 1) {
         int y = 0;
         if (t < S && t >= o) y = s_scan[t - o];
@@ -183,7 +228,7 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
             }
             p.hv[t] = v;
             p.tag[v] = 0;
-            for (int kk = 0; kk < nch; ++kk) p.chunks[c0 + kk] = make_int4(v, kk, nch, t);
+            emit_chunks(p, c0, v, t, nch, rb, re);
             if (MODE == kModeSpd) {
                 p.sigma[(size_t)v * S + t] = 1.0;
                 long long sl = -1;
@@ -209,7 +254,9 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
     }
 }
 
-// Expansion of level L (forward pass, Section 2 / Section 4.1).
+// Expansion of level L (forward pass, Section 2 / Section 4.1). Lane l holds
+// sources l + 32 i; the next 32 heads are fetched while the current ones'
+// masks are read.
 template <int W, int MODE>
 __device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
                               long long cs1, unsigned long long &my_edges, const uint64_t *s_need,
@@ -222,14 +269,24 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
     const int stride = p.vs_stride;
     const int CH = p.chunk_arcs;
     for (long long c = gwarp; c < ccnt; c += nwarps) {
-        const int4 ch = p.chunks[cs + c];
-        const int v = ch.x, k = ch.y, e = ch.w;
+        const Chunk ch = load_chunk(&p.chunks[cs + c]);
+        const int v = ch.v, e = ch.e;
+        const long long a0 = ch.a0;
+        const int na = ch.na;
+        int wv_next = lane < na ? p.col[a0 + lane] : 0;
         const uint64_t *vrow = p.vs + (size_t)v * stride;
         uint64_t F[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
-        const long long rb = p.off[v], re = p.off[v + 1];
-        if (k == 0) {
+        double sig[PL];
+        if (MODE == kModeSpd) {
+#pragma unroll
+            for (int ii = 0; ii < PL; ++ii) sig[ii] = p.sigma[(size_t)v * S + lane + 32 * ii];
+#pragma unroll
+            for (int ii = 0; ii < PL; ++ii)
+                if (!mask_bit<W>(F, lane + 32 * ii)) sig[ii] = 0.0;
+        }
+        if (ch.k == 0) {
 #pragma unroll
             for (int w = 0; w < W; ++w)
                 if (lane == w) p.hm[(size_t)e * W + w] = F[w];
@@ -243,7 +300,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     int pc = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
-                    my_edges += (unsigned long long)pc * (unsigned long long)(re - rb);
+                    my_edges += (unsigned long long)pc * (unsigned long long)(p.off[v + 1] - p.off[v]);
                 }
                 const uint64_t qm = p.qmask[v];
 #pragma unroll
@@ -258,30 +315,19 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                                 p.qlevel[s * 64 + q] = L;
                             }
                         }
-                        if (p.sigma[(size_t)v * S + s] >= 9007199254740992.0)
+                        if (sig[ii] >= 9007199254740992.0)
                             atomicOr((unsigned long long *)&p.srcflag[s >> 6], 1ull << (s & 63));
                     }
                 }
             }
         }
-        double sig[PL];
-        if (MODE == kModeSpd) {
-#pragma unroll
-            for (int ii = 0; ii < PL; ++ii) {
-                const int s = lane + 32 * ii;
-                sig[ii] = mask_bit<W>(F, s) ? p.sigma[(size_t)v * S + s] : 0.0;
-            }
-        }
-        const long long a0 = rb + (long long)k * CH;
-        const long long a1 = min(re, a0 + CH);
-        for (long long base = a0; base < a1; base += 32) {
-            const long long idx = base + lane;
-            const bool valid = idx < a1;
-            int wv = 0;
+        for (int base = 0; base < na; base += 32) {
+            const bool valid = base + lane < na;
+            const int wv = wv_next;
+            wv_next = base + 32 + lane < na ? p.col[a0 + base + 32 + lane] : 0;
             uint64_t nm[W];
             bool any = false;
             if (valid) {
-                wv = p.col[idx];
                 const uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -294,6 +340,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
             }
             bool app = false;
             int wnch = 0;
+            long long wrb = 0, wre = 0;
             if (any) {
                 uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
@@ -302,11 +349,12 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                 const int old = atomicMax(&p.tag[wv], L + 1);
                 app = old < L + 1;
                 if (app) {
-                    const long long d = p.off[wv + 1] - p.off[wv];
-                    wnch = (int)max(1ll, (d + CH - 1) / CH);
+                    wrb = p.off[wv];
+                    wre = p.off[wv + 1];
+                    wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
                 }
             }
-            warp_append<W, MODE>(p, L, app, wv, wnch, es1, cs1, lane);
+            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
             if (MODE == kModeSpd) {
                 unsigned bal = __ballot_sync(kFull, any);
                 while (bal) {
@@ -329,6 +377,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
 }
 
 // delta for the (v, F) entry once its sum of c over tight out-arcs is known.
+// Lane l holds the source pairs (64 k + 2 l, 64 k + 2 l + 1), k < W.
 template <int W>
 __device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const uint64_t (&F)[W],
                                                const double (&acc)[2 * W], const uint64_t *s_need, int lane) {
@@ -336,39 +385,48 @@ __device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const
     const uint64_t qm = p.qmask[v];
     double *row = p.sigma + (size_t)v * S;
 #pragma unroll
-    for (int ii = 0; ii < 2 * W; ++ii) {
-        const int s = lane + 32 * ii;
-        if (mask_bit<W>(F, s)) {
-            const double sv = row[s];
-            const double d = sv * acc[ii];
-            row[s] = (1.0 + d) / sv;
-            if (qm) {
-                uint64_t x = qm & s_need[s];
-                while (x) {
-                    const int q = __ffsll((long long)x) - 1;
-                    x &= x - 1;
-                    p.dep[s * 64 + q] = d;
+    for (int k = 0; k < W; ++k) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int s = 64 * k + 2 * lane + j;
+            if ((F[k] >> (2 * lane + j)) & 1ull) {
+                const double sv = row[s];
+                const double d = sv * acc[2 * k + j];
+                row[s] = (1.0 + d) / sv;
+                if (qm) {
+                    uint64_t x = qm & s_need[s];
+                    while (x) {
+                        const int q = __ffsll((long long)x) - 1;
+                        x &= x - 1;
+                        p.dep[s * 64 + q] = d;
+                    }
                 }
             }
         }
     }
 }
 
-// Eq. 4 for the entries of level L (backward pass).
+// Eq. 4 for the entries of level L (backward pass). The c rows of up to NB
+// tight heads are copied into the warp's shared-memory stage with 16-byte
+// cp.async transfers (one source pair per lane and mask word), then summed
+// in arc order.
 template <int W>
 __device__ void backward_level(const TravParams &p, int L, long long cs, long long ccnt,
                                const uint64_t *s_active, const uint64_t *s_need, long long gwarp,
-                               long long nwarps) {
+                               long long nwarps, double *stage) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
-    constexpr int G = (W >= 4) ? 1 : 4 / W;  // arcs gathered before their adds
+    constexpr int NB = kStageBytes / (8 * S);
+    static_assert(NB >= 1 && NB <= 16, "stage holds 1..16 rows");
     const int lane = threadIdx.x & 31;
     const int nx = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
-    const int CH = p.chunk_arcs;
     for (long long c = gwarp; c < ccnt; c += nwarps) {
-        const int4 ch = p.chunks[cs + c];
-        const int v = ch.x, k = ch.y, nch = ch.z, e = ch.w;
+        const Chunk ch = load_chunk(&p.chunks[cs + c]);
+        const int v = ch.v, e = ch.e, k = ch.k, nch = ch.nch;
+        const long long a0 = ch.a0;
+        const int na = ch.na;
+        int wv_next = lane < na ? p.col[a0 + lane] : 0;
         uint64_t F[W];
         bool anyF = false;
 #pragma unroll
@@ -380,16 +438,13 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
         double acc[PL];
 #pragma unroll
         for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
-        const long long rb = p.off[v], re = p.off[v + 1];
-        const long long a0 = rb + (long long)k * CH;
-        const long long a1 = min(re, a0 + CH);
-        for (long long base = a0; base < a1; base += 32) {
-            const long long idx = base + lane;
-            int wv = 0;
+        for (int base = 0; base < na; base += 32) {
+            const bool valid = base + lane < na;
+            const int wv = wv_next;
+            wv_next = base + 32 + lane < na ? p.col[a0 + base + 32 + lane] : 0;
             uint64_t tm[W];
             bool any = false;
-            if (idx < a1) {
-                wv = p.col[idx];
+            if (valid) {
                 const uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
                 for (int w = 0; w < W; ++w) {
@@ -402,30 +457,40 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
             }
             unsigned bal = __ballot_sync(kFull, any);
             while (bal) {
-                double val[G][PL];
+                unsigned bits[W];
 #pragma unroll
-                for (int gi = 0; gi < G; ++gi) {
+                for (int w = 0; w < W; ++w) bits[w] = 0u;
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
                     int i = -1;
                     if (bal) {
                         i = __ffs(bal) - 1;
                         bal &= bal - 1;
                     }
-                    const int src_lane = i < 0 ? 0 : i;
-                    const int wi = __shfl_sync(kFull, wv, src_lane);
-                    uint64_t tmi[W];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) tmi[w] = __shfl_sync(kFull, tm[w], src_lane);
+                    const int sl = i < 0 ? 0 : i;
+                    const int wi = __shfl_sync(kFull, wv, sl);
                     const double *crow = p.sigma + (size_t)wi * S;
 #pragma unroll
-                    for (int ii = 0; ii < PL; ++ii) {
-                        const int s = lane + 32 * ii;
-                        val[gi][ii] = (i >= 0 && mask_bit<W>(tmi, s)) ? crow[s] : 0.0;
+                    for (int w = 0; w < W; ++w) {
+                        const uint64_t tmi = __shfl_sync(kFull, tm[w], sl);
+                        const unsigned two = i < 0 ? 0u : (unsigned)((tmi >> (2 * lane)) & 3ull);
+                        bits[w] |= two << (2 * b);
+                        cp_async16(stage + b * S + 64 * w + 2 * lane, crow + 64 * w + 2 * lane, two ? 16 : 0);
                     }
                 }
+                cp_async_wait_all();
+                __syncwarp();
 #pragma unroll
-                for (int gi = 0; gi < G; ++gi)
+                for (int b = 0; b < NB; ++b) {
 #pragma unroll
-                    for (int ii = 0; ii < PL; ++ii) acc[ii] += val[gi][ii];
+                    for (int w = 0; w < W; ++w) {
+                        const unsigned two = (bits[w] >> (2 * b)) & 3u;
+                        const double2 val = *reinterpret_cast<const double2 *>(stage + b * S + 64 * w + 2 * lane);
+                        if (two & 1u) acc[2 * w] += val.x;
+                        if (two & 2u) acc[2 * w + 1] += val.y;
+                    }
+                }
+                __syncwarp();
             }
         }
         if (nch == 1) {
@@ -434,7 +499,8 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
             const long long slot0 = p.hslot[e];
             double *prow = p.partial + (size_t)(slot0 + k) * S;
 #pragma unroll
-            for (int ii = 0; ii < PL; ++ii) __stcg(&prow[lane + 32 * ii], acc[ii]);
+            for (int w = 0; w < W; ++w)
+                __stcg(reinterpret_cast<double2 *>(prow + 64 * w + 2 * lane), make_double2(acc[2 * w], acc[2 * w + 1]));
             __threadfence();
             int prev = 0;
             if (lane == 0) prev = atomicAdd(&p.pdone[slot0], 1);
@@ -446,7 +512,11 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
                 for (int kk = 0; kk < nch; ++kk) {
                     const double *q = p.partial + (size_t)(slot0 + kk) * S;
 #pragma unroll
-                    for (int ii = 0; ii < PL; ++ii) acc[ii] += __ldcg(&q[lane + 32 * ii]);
+                    for (int w = 0; w < W; ++w) {
+                        const double2 x = __ldcg(reinterpret_cast<const double2 *>(q + 64 * w + 2 * lane));
+                        acc[2 * w] += x.x;
+                        acc[2 * w + 1] += x.y;
+                    }
                 }
                 if (lane == 0) p.pdone[slot0] = 0;
                 finalize_entry<W>(p, v, F, acc, s_need, lane);
@@ -455,21 +525,31 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
     }
 }
 
+template <int W>
+struct KernelShape {
+    static constexpr int kMinBlocks = W >= 4 ? 1 : 2;
+};
+
 template <int W, int MODE>
-__global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
+__global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(TravParams p) {
     constexpr int S = 64 * W;
+    extern __shared__ __align__(16) double s_stage_all[];
     const int lane = threadIdx.x & 31;
     const long long wpb = blockDim.x >> 5;
     const long long gwarp = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
     const long long nwarps = (long long)gridDim.x * wpb;
     const long long gthr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
+    double *stage = s_stage_all + (threadIdx.x >> 5) * (kStageBytes / 8);
     uint32_t gen = 0;
     __shared__ uint64_t s_need[S];
     __shared__ int32_t s_minql[S];
     __shared__ uint64_t s_active[W];
     __shared__ int32_t s_lstop;
     unsigned long long my_edges = 0;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_mark = timer ? global_ns() : 0ull;
+    unsigned long long ns_fwd = 0, ns_bwd = 0, ns_other = 0;
 
     for (long long tile = 0; tile < p.ntiles; ++tile) {
         const int32_t *tsrc = p.srcs + tile * S;
@@ -479,6 +559,11 @@ __global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
             s_need[s] = (MODE == kModeSpd && v >= 0) ? p.need[v] : 0ull;
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        if (timer) {
+            const unsigned long long t = global_ns();
+            ns_other += t - t_mark;
+            t_mark = t;
+        }
 
         // ---------------- forward ----------------
         long long es = 0, cs = 0, es_prev = 0;
@@ -518,7 +603,12 @@ __global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
             ++L;
         }
         const int Lmax = L;
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicMax(&p.ctr->levels_max, (unsigned long long)Lmax);
+        if (timer) {
+            const unsigned long long t = global_ns();
+            ns_fwd += t - t_mark;
+            t_mark = t;
+            atomicMax(&p.ctr->levels_max, (unsigned long long)Lmax);
+        }
 
         // ---------------- backward ----------------
         if (MODE == kModeSpd && !(p.flags & kFlagNoBackward)) {
@@ -571,10 +661,15 @@ __global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
                             atomicOr((unsigned long long *)&row[cur * W + w], (unsigned long long)p.hm[e * W + w]);
                     }
                 }
-                backward_level<W>(p, Lb, p.lev_cstart[Lb], (long long)p.lev_ccnt[Lb], s_active, s_need, gwarp,
-                                  nwarps);
+                backward_level<W>(p, Lb, p.lev_cstart[Lb], (long long)p.lev_ccnt[Lb], s_active, s_need, gwarp, nwarps,
+                                  stage);
                 if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
+        }
+        if (timer) {
+            const unsigned long long t = global_ns();
+            ns_bwd += t - t_mark;
+            t_mark = t;
         }
 
         // ---------------- tile end ----------------
@@ -629,22 +724,34 @@ __global__ void __launch_bounds__(512) trav_kernel(TravParams p) {
             }
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        if (timer) {
+            const unsigned long long t = global_ns();
+            ns_other += t - t_mark;
+            t_mark = t;
+        }
     }
-    // fold per-thread edge counts
     if (MODE == kModeSpd && my_edges) atomicAdd(&p.ctr->edges, my_edges);
+    if (timer) {
+        p.ctr->ns_fwd += ns_fwd;
+        p.ctr->ns_bwd += ns_bwd;
+        p.ctr->ns_other += ns_other;
+    }
 }
 
 template <int W, int MODE>
 bc_status launch(bc_graph *g, TravParams &p) {
     auto kern = trav_kernel<W, MODE>;
-    int threads = g->block_threads;
+    const int threads = g->block_threads;
+    const size_t smem = (size_t)(threads / 32) * kStageBytes;
+    BCD_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
+    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return set_error(BC_E_INTERNAL, "traversal kernel cannot be resident");
     dim3 grid((unsigned)(g->num_sms * per_sm)), block((unsigned)threads);
     void *args[] = {(void *)&p};
-    BCD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, grid, block, args, 0, g->stream));
+    BCD_CUDA(cudaLaunchCooperativeKernel((const void *)kern, grid, block, args, smem, g->stream));
     g->launches += 1;
+    g->last_grid = (int)grid.x;
     return BC_OK;
 }
 
@@ -707,6 +814,9 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         if (c.err == kDevOk) {
             if (levels_out) *levels_out = (int)c.levels_max;
             if (edges_out) *edges_out = c.edges;
+            g->last_ns_fwd = c.ns_fwd;
+            g->last_ns_bwd = c.ns_bwd;
+            g->last_ns_other = c.ns_other;
             return BC_OK;
         }
         if (c.err == kDevTimeout) {
