@@ -229,14 +229,18 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
  *   chunk_arcs     arcs per unit of work when a vertex's row is split
  *                  (32..65536, a multiple of 32);
  *   block_threads  threads per block of the persistent kernel (128..512,
- *                  a multiple of 32).
+ *                  a multiple of 32);
+ *   source_order   how the union of sources is cut into tiles: 1 (default)
+ *                  groups sources by their hop distance to the vertex of
+ *                  largest in-degree x out-degree, so that a tile's BFS
+ *                  levels line up; 2 keeps ascending vertex ids.
  * Zero fields keep their current value.
  */
 typedef struct {
     int32_t tile_words;
     int32_t chunk_arcs;
     int32_t block_threads;
-    int32_t reserved;
+    int32_t source_order;
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);

@@ -107,6 +107,7 @@ struct TravParams {
     uint64_t *srcflag;       // [W] sigma >= 2^53 seen for a source slot (this tile)
     // reach mode output
     uint64_t *rvmask;        // [n]
+    int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
     Counters *ctr;
     double timeout_ns;
 };
@@ -146,6 +147,8 @@ struct bcd_workspace {
     uint64_t *need = nullptr;     // [n]
     uint64_t *qmask = nullptr;    // [n]
     int32_t *posd = nullptr;      // [n] position of a vertex in the source union
+    int32_t *hublev = nullptr;    // [n] hop distance to the hub (tile ordering key), -1 unreached
+    int32_t hub = -1;             // vertex the ordering key is measured to
     int32_t *dlist = nullptr;     // [n + 64*4] source union, padded to whole tiles
     int32_t *qlevel = nullptr;    // [256 * 64]
     double *dep = nullptr;        // [256 * 64]
@@ -194,8 +197,10 @@ struct bc_graph {
     uint32_t *d_rw = nullptr;
     std::vector<int64_t> h_off;   // forward offsets (degree checks)
     std::vector<int64_t> h_roff;  // reverse offsets
+    std::vector<int32_t> h_hublev; // host copy of the tile ordering key
     int tile_words = 1;           // W of the SPD kernel
-    int chunk_arcs = 256;
+    int chunk_arcs = 128;
+    int source_order = 1;         // 1: tiles ordered by distance to the hub, 0: by vertex id
     int block_threads = 512;
     bcd_workspace ws;
     int64_t launches = 0;

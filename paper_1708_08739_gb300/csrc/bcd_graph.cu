@@ -123,6 +123,9 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
         return set_error(BC_E_INVALID_ARG, "bc_set_config: chunk_arcs must be a multiple of 32 in [32, 65536]");
     if (c->block_threads && (c->block_threads < 128 || c->block_threads > 512 || c->block_threads % 32))
         return set_error(BC_E_INVALID_ARG, "bc_set_config: block_threads must be a multiple of 32 in [128, 512]");
+    if (c->source_order && c->source_order != 1 && c->source_order != 2)
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: source_order must be 1 or 2");
+    if (c->source_order) g->source_order = c->source_order == 1 ? 1 : 0;
     if (c->tile_words) g->tile_words = c->tile_words;
     if (c->chunk_arcs) g->chunk_arcs = c->chunk_arcs;
     if (c->block_threads) g->block_threads = c->block_threads;
@@ -134,7 +137,7 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->tile_words = g->tile_words;
     c->chunk_arcs = g->chunk_arcs;
     c->block_threads = g->block_threads;
-    c->reserved = 0;
+    c->source_order = g->source_order == 1 ? 1 : 2;
     return BC_OK;
 }
 

@@ -134,6 +134,11 @@ __global__ void fill_i32(int32_t *p, int64_t cnt, int32_t val) {
         p[i] = val;
 }
 
+__global__ void positions(const int32_t *list, int64_t cnt, int32_t *pos) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+        pos[list[i]] = (int32_t)i;
+}
+
 // bc for each query bit: scale[q] * sum over tiles (pairwise, fixed order)
 __global__ void reduce_tiles(const double *tile_partial, int64_t ntiles, const double *scale, double *out) {
     __shared__ double s[256];
@@ -206,6 +211,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.need);
     dev_free(ws.qmask);
     dev_free(ws.posd);
+    dev_free(ws.hublev);
     dev_free(ws.dlist);
     dev_free(ws.qlevel);
     dev_free(ws.dep);
@@ -246,6 +252,8 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.need, (size_t)n));
     BCD_TRY(dev_alloc(&ws.qmask, (size_t)n));
     BCD_TRY(dev_alloc(&ws.posd, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.hublev, (size_t)n));
+    ws.hub = -1;
     BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 256));
     BCD_TRY(dev_alloc(&ws.qlevel, 256 * 64));
     BCD_TRY(dev_alloc(&ws.dep, 256 * 64));
@@ -389,6 +397,70 @@ static bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, cons
     return BC_OK;
 }
 
+// Tile ordering key: hop distance from each vertex to the hub, the vertex of
+// largest in-degree x out-degree (one reach traversal of R(G) from the hub,
+// cached per graph). Sources at equal distance to the hub have closely
+// aligned BFS level profiles, so a tile of them touches each vertex at fewer
+// distinct levels.
+static bc_status ensure_hub_levels(bc_graph *g) {
+    std::vector<int32_t> &h_lev = g->h_hublev;
+    bcd_workspace &ws = g->ws;
+    if (ws.hub >= 0 && (int64_t)h_lev.size() == g->n) return BC_OK;
+    int32_t hub = 0;
+    long long best = -1;
+    for (int32_t v = 0; v < g->n; ++v) {
+        const long long prod = (long long)(g->h_off[v + 1] - g->h_off[v]) * (g->h_roff[v + 1] - g->h_roff[v]);
+        if (prod > best) {
+            best = prod;
+            hub = v;
+        }
+    }
+    cudaStream_t s = g->stream;
+    BCD_CUDA(cudaMemsetAsync(ws.hublev, 0xff, sizeof(int32_t) * (size_t)g->n, s));
+    BCD_CUDA(cudaMemsetAsync(ws.rvmask, 0, sizeof(uint64_t) * (size_t)g->n, s));
+    std::vector<int32_t> tsrc(64, -1);
+    tsrc[0] = hub;
+    BCD_CUDA(cudaMemcpyAsync(ws.dlist, tsrc.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeReach;
+    p.off = g->d_roff;
+    p.col = g->d_rcol;
+    p.srcs = ws.dlist;
+    p.ntiles = 1;
+    p.rvmask = ws.rvmask;
+    p.levout = ws.hublev;
+    BCD_TRY(run_traversal(g, 1, p, nullptr, nullptr));
+    h_lev.resize((size_t)g->n);
+    BCD_CUDA(cudaMemcpyAsync(h_lev.data(), ws.hublev, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaStreamSynchronize(s));
+    ws.hub = hub;
+    return BC_OK;
+}
+
+// Stable reorder of the source union by hub distance (unreached last).
+static bc_status order_sources(bc_graph *g, int64_t nd) {
+    bcd_workspace &ws = g->ws;
+    BCD_TRY(ensure_hub_levels(g));
+    const std::vector<int32_t> &h_lev = g->h_hublev;
+    cudaStream_t s = g->stream;
+    std::vector<int32_t> d((size_t)nd), out((size_t)nd);
+    BCD_CUDA(cudaMemcpyAsync(d.data(), ws.dlist, sizeof(int32_t) * (size_t)nd, cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaStreamSynchronize(s));
+    int32_t maxk = 0;
+    for (int64_t i = 0; i < nd; ++i) maxk = std::max(maxk, h_lev[d[i]]);
+    std::vector<int64_t> cnt((size_t)maxk + 3, 0);
+    auto key = [&](int32_t v) { return h_lev[v] < 0 ? maxk + 1 : h_lev[v]; };
+    for (int64_t i = 0; i < nd; ++i) cnt[key(d[i]) + 1]++;
+    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
+    for (int64_t i = 0; i < nd; ++i) out[cnt[key(d[i])]++] = d[i];
+    BCD_CUDA(cudaMemcpyAsync(ws.dlist, out.data(), sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, s));
+    positions<<<grid_for(g, nd, 256), 256, 0, s>>>(ws.dlist, nd, ws.posd);
+    g->launches += 1;
+    BCD_CUDA(cudaStreamSynchronize(s));
+    return BC_OK;
+}
+
 static double samples_for(double eps, double delta) { return std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps)); }
 
 // Runs one group of at most 64 queries whose out-degree is positive.
@@ -471,6 +543,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     BCD_CUDA(cudaMemcpyAsync(&nd, d_cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaStreamSynchronize(s));
     const int64_t ntiles = (nd + S - 1) / S;
+    if (g->source_order == 1 && ntiles >= 2) BCD_TRY(order_sources(g, nd));
     if (ntiles * S > nd) {
         fill_i32<<<1, 256, 0, s>>>(ws.dlist + nd, ntiles * S - nd, -1);
         g->launches += 1;

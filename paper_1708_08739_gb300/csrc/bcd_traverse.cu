@@ -287,6 +287,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                 if (!mask_bit<W>(F, lane + 32 * ii)) sig[ii] = 0.0;
         }
         if (ch.k == 0) {
+            if (MODE == kModeReach && p.levout && lane == 0 && p.levout[v] < 0) p.levout[v] = L;
 #pragma unroll
             for (int w = 0; w < W; ++w)
                 if (lane == w) p.hm[(size_t)e * W + w] = F[w];
