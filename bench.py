@@ -1,0 +1,313 @@
+"""Benchmark: batched exact BC(r) on a directed R-MAT scale-20 graph.
+
+Workload (one step): one bc_batch call of 64 exact queries (32 uniform random
+vertices and the 32 vertices of largest in-degree x out-degree) on R-MAT
+scale 20, edge factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, self-loops and
+repeated arcs removed, unweighted. The metric is BC(r) queries per second;
+GTEPS (sum over sources of the arcs they reach, per second) is reported too.
+
+Arms:
+  default            the CUDA library (libbcd.so) on one GPU per rank; under
+                     torchrun every rank solves its own copy of the batch
+                     (independent problems, weak scaling, no collective on
+                     the data path; the step time is the max over ranks).
+  --impl reference   the CPU oracle as it stands, on the host cores, on a
+                     bounded sample of the same batch's sources.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+METRIC = "GTEPS and BC(r) queries/s (exact and sampled) vs HBM roofline; p50/p99 query latency"
+WORKLOAD = "rmat20_ef16_exact64"
+# dram bytes per (source x reached arc) of the traversal kernel, from the ncu
+# capture summarised in profiles/trav_kernel_rmat20.md; None when the kernel
+# has changed since that capture
+TRAFFIC_BYTES_PER_EDGE = None
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload():
+    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
+    qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
+    return g, qs
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "bcd_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_union(g, qs):
+    """The union D of RV(r) over the batch's queries, by the oracle."""
+    import oracle as O
+    og = O.Graph.from_csr(g)
+    union = set()
+    outd = g.out_degree()
+    for r in sorted(set(qs)):
+        if outd[r] > 0:
+            union.update(O.rv(og, r).tolist())
+    return og, np.array(sorted(union), dtype=np.int32)
+
+
+def oracle_sample(og, D, qs, n_sources, threads, seed=7):
+    """Times the oracle on a sample of the batch's sources: delta_s.(r_q) for
+    every query q and sampled source s. Returns (seconds, sources timed)."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(D.shape[0], size=min(n_sources, D.shape[0]), replace=False))
+    srcs = D[pick]
+    t = time.time()
+    O.dependencies(og, srcs, np.array(qs, dtype=np.int32), nthreads=threads)
+    return time.time() - t, int(srcs.shape[0])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    g, qs = make_workload()
+    threads = os.cpu_count() or 1
+    per_step = 64
+    og, D = oracle_union(g, qs)
+    nd = int(D.shape[0])
+    times = []
+    for i in range(args.warmup + args.steps):
+        el, ns = oracle_sample(og, D, qs, per_step, threads, seed=i)
+        if i >= args.warmup:
+            times.append(el / ns)
+    t_src = sum(times) / len(times)
+    qps = len(qs) / (t_src * nd)
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(qs) / qps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "queries": len(qs), "sources_in_union": nd},
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d of the %d union sources per step, all 64 queries; queries/s = 64 / "
+                                       "(seconds per source x union size)" % (per_step, nd)},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_08739_gb300 as bcd
+
+    t0 = time.time()
+    g, qs = make_workload()
+    log("workload built in %.1fs: n=%d m=%d" % (time.time() - t0, g.n, g.m))
+    stream = torch.cuda.Stream()
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, stream=stream.cuda_stream)
+    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    specs = [{"r": r} for r in qs]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        t = time.time()
+        out, info = bcd.bc_batch(dg, specs)
+        log("warmup %d: %.2fs" % (i, time.time() - t))
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for i in range(args.steps):
+        out, info = bcd.bc_batch(dg, specs)
+        infos.append(info)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nq = len(qs)
+    qps = world * nq / (ms / 1000.0)
+    edges = float(np.mean([i["edges_traversed"] for i in infos]))
+    gteps = world * edges / (ms / 1000.0) / 1e9
+    trav_ms = float(np.mean([i["ms_traversal"] for i in infos]))
+    reached = float(np.mean([i["reached_pairs"] for i in infos]))
+    tight = float(np.mean([i["tight_pairs"] for i in infos]))
+    vb = float(np.mean([i["union_vertices"] for i in infos]))
+    eb = float(np.mean([i["union_arcs"] for i in infos]))
+    launches = int(sum(i["launches"] for i in infos) / args.steps)
+    algo_bytes = 2.0 * (8.0 * vb + 4.0 * eb) + 40.0 * reached + 24.0 * tight
+    peak, peak_kind = peaks()
+    achieved = algo_bytes / (trav_ms / 1000.0) / 1e9
+    traffic = None if TRAFFIC_BYTES_PER_EDGE is None else TRAFFIC_BYTES_PER_EDGE * edges
+
+    # end to end through the C ABI: pinned host CSR in, results out
+    off_h = torch.from_numpy(g.offsets).pin_memory()
+    col_h = torch.from_numpy(g.cols).pin_memory()
+    barrier()
+    t = time.time()
+    ge = bcd.bc_graph_create(g.n, off_h.numpy(), col_h.numpy(), stream=stream.cuda_stream)
+    bcd.bc_set_config(ge, tile_words=args.tile_words)
+    out_e, info_e = bcd.bc_batch(ge, specs)
+    ge.close()
+    barrier()
+    e2e_s = time.time() - t
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    h2d = g.offsets.nbytes + g.cols.nbytes + nq * 40
+    d2h = nq * 32
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        og, D = oracle_union(g, qs)
+        nd = int(D.shape[0])
+        el, ns = oracle_sample(og, D, qs, args.cpu_sources, threads)
+        t_src = el / ns
+        cpu = {"value": nq / (t_src * nd), "unit": "queries/s", "cores": threads, "kind": "oracle",
+               "sample": "%d of the %d union sources, delta for all 64 queries; queries/s = 64 / "
+                         "(seconds per source x union size)" % (ns, nd)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": "R-MAT scale 20, edge factor 16, a/b/c/d 0.57/0.19/0.19/0.05, "
+                                                  "seed 20, loops and repeats removed, unweighted",
+                       "n": g.n, "m": g.m, "queries": nq,
+                       "query_mix": "32 uniform (seed 103) + 32 top in-degree x out-degree, exact",
+                       "tile_words": args.tile_words, "sources_in_union": int(infos[-1]["sources_run"]),
+                       "l2": "not flushed: working set (sigma slab, graph, level history) well above L2",
+                       "parallelism": "replicas: each rank solves its own batch"},
+            "gteps": gteps,
+            "phases_ms": {"rv": float(np.mean([i["ms_rv"] for i in infos])),
+                          "sample": float(np.mean([i["ms_sample"] for i in infos])),
+                          "traversal": trav_ms,
+                          "forward": float(np.mean([i["ms_forward"] for i in infos])),
+                          "backward": float(np.mean([i["ms_backward"] for i in infos]))},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "trav_kernel (batched SPD + dependency traversal)",
+                         "algorithmic_bytes": algo_bytes},
+            "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "check": {"bc_first": out[0]["bc"], "e2e_equal": all(abs(a["bc"] - b["bc"]) <= 1e-9 * max(1, abs(b["bc"]))
+                                                                  for a, b in zip(out_e, out))},
+        }
+        print(json.dumps(line), flush=True)
+    dg.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tile-words", type=int, default=2)
+    ap.add_argument("--cpu-sources", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

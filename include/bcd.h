@@ -195,6 +195,12 @@ typedef struct {
     int64_t tiles;            /* tiles of 64*tile_words sources run */
     int32_t max_level;        /* deepest SPD level met */
     int32_t grid_blocks;      /* blocks of the persistent traversal launch */
+    double ms_traversal;      /* CUDA-event time of the batched traversal launches */
+    int64_t reached_pairs;    /* sum over sources s of |V_s| (vertices s reaches) */
+    int64_t tight_pairs;      /* sum over sources s of the arcs of s's SPD */
+    int64_t arc_visits;       /* arcs scanned by the traversal, both passes */
+    int64_t union_vertices;   /* sum over tiles of vertices any tile source reaches */
+    int64_t union_arcs;       /* sum over tiles of the out-arcs of those vertices */
 } bc_batch_info;
 
 /*

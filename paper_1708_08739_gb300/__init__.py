@@ -66,7 +66,9 @@ class bc_batch_info(C.Structure):
                 ("launches", C.c_int64), ("ms_rv", C.c_double), ("ms_sample", C.c_double),
                 ("ms_spd", C.c_double), ("ms_total", C.c_double), ("ms_forward", C.c_double),
                 ("ms_backward", C.c_double), ("tiles", C.c_int64), ("max_level", C.c_int32),
-                ("grid_blocks", C.c_int32)]
+                ("grid_blocks", C.c_int32), ("ms_traversal", C.c_double), ("reached_pairs", C.c_int64),
+                ("tight_pairs", C.c_int64), ("arc_visits", C.c_int64), ("union_vertices", C.c_int64),
+                ("union_arcs", C.c_int64)]
 
 
 class bc_config(C.Structure):

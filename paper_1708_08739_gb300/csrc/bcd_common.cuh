@@ -36,6 +36,11 @@ struct Counters {
     unsigned long long ns_fwd;     // block 0's wall time in forward passes
     unsigned long long ns_bwd;     // ... in backward passes
     unsigned long long ns_other;   // ... in tile set-up and tear-down
+    unsigned long long reached;    // sum over sources s of |V_s| (vertices s reaches, s included)
+    unsigned long long tight;      // sum over sources s of tight arcs (sigma additions)
+    unsigned long long arc_visits; // arcs scanned, forward plus backward
+    unsigned long long vb;         // sum over tiles of distinct vertices reached
+    unsigned long long eb;         // sum over tiles of the out-arcs of those vertices
 };
 
 // One unit of expansion work: arcs [a0, a0 + na) of vertex v, the k-th of
@@ -208,6 +213,8 @@ struct bc_graph {
     unsigned long long last_ns_fwd = 0;      // phase times of the last traversal launch
     unsigned long long last_ns_bwd = 0;
     unsigned long long last_ns_other = 0;
+    bcd::Counters last;                           // counters of the last traversal launch
+    float last_ms_launch = 0;                // CUDA-event time of the last traversal launch
 };
 
 namespace bcd {

@@ -302,7 +302,8 @@ struct GQuery {
 
 struct GroupTimes {
     float rv = 0, sample = 0, spd = 0, total = 0;
-    double fwd = 0, bwd = 0;
+    double fwd = 0, bwd = 0, trav = 0;
+    bcd::Counters c{};
     int64_t sources = 0;
     int64_t tiles = 0;
     unsigned long long edges = 0;
@@ -470,6 +471,8 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     const int nq = (int)qs.size();
     const int W = g->tile_words;
     const int S = 64 * W;
+    // the ordering key's reach traversal uses the union buffer: run it first
+    if (g->source_order == 1) BCD_TRY(ensure_hub_levels(g));
     Events ev(s);
     ev.rec(0);
     // distinct roots
@@ -595,6 +598,8 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         BCD_TRY(run_traversal(g, W, p, &levels, &edges));
         tm.fwd = g->last_ns_fwd * 1e-6;
         tm.bwd = g->last_ns_bwd * 1e-6;
+        tm.trav = g->last_ms_launch;
+        tm.c = g->last;
         std::vector<double> scale(64, 1.0);
         for (int i = 0; i < nq; ++i)
             if (qs[i].sampled && qs[i].rv > 0) scale[i] = (double)qs[i].rv / (double)qs[i].T;
@@ -666,6 +671,12 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.tiles += t.tiles;
         bi.max_level = std::max(bi.max_level, (int32_t)t.levels);
         bi.grid_blocks = g->last_grid;
+        bi.ms_traversal += t.trav;
+        bi.reached_pairs += (int64_t)t.c.reached;
+        bi.tight_pairs += (int64_t)t.c.tight;
+        bi.arc_visits += (int64_t)t.c.arc_visits;
+        bi.union_vertices += (int64_t)t.c.vb;
+        bi.union_arcs += (int64_t)t.c.eb;
         group.clear();
         return BC_OK;
     };

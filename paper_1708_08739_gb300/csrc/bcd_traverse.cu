@@ -230,6 +230,10 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
             p.tag[v] = 0;
             emit_chunks(p, c0, v, t, nch, rb, re);
             if (MODE == kModeSpd) {
+                atomicAdd(&p.ctr->vb, 1ull);
+                atomicAdd(&p.ctr->eb, (unsigned long long)(re - rb));
+            }
+            if (MODE == kModeSpd) {
                 p.sigma[(size_t)v * S + t] = 1.0;
                 long long sl = -1;
                 if (nch > 1) {
@@ -257,9 +261,30 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
 // Expansion of level L (forward pass, Section 2 / Section 4.1). Lane l holds
 // sources l + 32 i; the next 32 heads are fetched while the current ones'
 // masks are read.
+// Per-thread work counters (32-bit; flushed to the 64-bit launch totals at
+// the end of every tile).
+struct Stats {
+    unsigned edges = 0, reached = 0, tight = 0, arcs = 0, vb = 0, eb = 0;
+};
+
+__device__ __forceinline__ void flush_stats(Counters *c, Stats &st, int lane) {
+    unsigned long long v[6] = {st.edges, st.reached, st.tight, st.arcs, st.vb, st.eb};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(kFull, v[i], o);
+    if (lane == 0) {
+        unsigned long long *dst[6] = {&c->edges, &c->reached, &c->tight, &c->arc_visits, &c->vb, &c->eb};
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            if (v[i]) atomicAdd(dst[i], v[i]);
+    }
+    st = Stats();
+}
+
 template <int W, int MODE>
 __device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
-                              long long cs1, unsigned long long &my_edges, const uint64_t *s_need,
+                              long long cs1, Stats &st, const uint64_t *s_need,
                               long long gwarp, long long nwarps) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
@@ -301,7 +326,8 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     int pc = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
-                    my_edges += (unsigned long long)pc * (unsigned long long)(p.off[v + 1] - p.off[v]);
+                    st.edges += (unsigned)pc * (unsigned)(p.off[v + 1] - p.off[v]);
+                    st.reached += (unsigned)pc;
                 }
                 const uint64_t qm = p.qmask[v];
 #pragma unroll
@@ -335,6 +361,11 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     nm[w] = F[w] & ~(wrow[w] | wrow[cur * W + w]);
                     any |= nm[w] != 0ull;
                 }
+                if (MODE == kModeSpd) {
+                    st.arcs += 1;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) st.tight += (unsigned)__popcll(nm[w]);
+                }
             } else {
 #pragma unroll
                 for (int w = 0; w < W; ++w) nm[w] = 0ull;
@@ -353,6 +384,10 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     wrb = p.off[wv];
                     wre = p.off[wv + 1];
                     wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
+                    if (MODE == kModeSpd && old < 0) {
+                        st.vb += 1;
+                        st.eb += (unsigned)(wre - wrb);
+                    }
                 }
             }
             warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
@@ -414,7 +449,7 @@ __device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const
 template <int W>
 __device__ void backward_level(const TravParams &p, int L, long long cs, long long ccnt,
                                const uint64_t *s_active, const uint64_t *s_need, long long gwarp,
-                               long long nwarps, double *stage) {
+                               long long nwarps, double *stage, Stats &st) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
     constexpr int NB = kStageBytes / (8 * S);
@@ -452,6 +487,7 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
                     tm[w] = F[w] & wrow[nx * W + w];
                     any |= tm[w] != 0ull;
                 }
+                st.arcs += 1;
             } else {
 #pragma unroll
                 for (int w = 0; w < W; ++w) tm[w] = 0ull;
@@ -547,7 +583,7 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
     __shared__ int32_t s_minql[S];
     __shared__ uint64_t s_active[W];
     __shared__ int32_t s_lstop;
-    unsigned long long my_edges = 0;
+    Stats st;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_mark = timer ? global_ns() : 0ull;
     unsigned long long ns_fwd = 0, ns_bwd = 0, ns_other = 0;
@@ -590,7 +626,7 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
                         atomicAnd((unsigned long long *)&row[nxt * W + w], ~(unsigned long long)p.hm[e * W + w]);
                 }
             }
-            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, my_edges, s_need, gwarp, nwarps);
+            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, st, s_need, gwarp, nwarps);
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             total = es1;
             if (ld_vol(&p.lev_cnt[L + 1]) == 0ull) break;
@@ -663,7 +699,7 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
                     }
                 }
                 backward_level<W>(p, Lb, p.lev_cstart[Lb], (long long)p.lev_ccnt[Lb], s_active, s_need, gwarp, nwarps,
-                                  stage);
+                                  stage, st);
                 if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
         }
@@ -672,6 +708,8 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
             ns_bwd += t - t_mark;
             t_mark = t;
         }
+
+        if (MODE == kModeSpd) flush_stats(p.ctr, st, lane);
 
         // ---------------- tile end ----------------
         if (MODE == kModeSpd && blockIdx.x == 0 && threadIdx.x < 64) {
@@ -731,7 +769,7 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
             t_mark = t;
         }
     }
-    if (MODE == kModeSpd && my_edges) atomicAdd(&p.ctr->edges, my_edges);
+
     if (timer) {
         p.ctr->ns_fwd += ns_fwd;
         p.ctr->ns_bwd += ns_bwd;
@@ -796,6 +834,9 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.timeout_ns = 10.0e9;
         BCD_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), g->stream));
         bc_status st = BC_E_INTERNAL;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        const bool timed = cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess;
+        if (timed) cudaEventRecord(ev0, g->stream);
         if (p.mode == kModeReach) {
             if (W != 1) return set_error(BC_E_INTERNAL, "reach traversal runs with one mask word");
             st = launch<1, kModeReach>(g, p);
@@ -808,11 +849,25 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         } else {
             return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
         }
-        if (st != BC_OK) return st;
+        if (timed) cudaEventRecord(ev1, g->stream);
+        if (st != BC_OK) {
+            if (timed) {
+                cudaEventDestroy(ev0);
+                cudaEventDestroy(ev1);
+            }
+            return st;
+        }
         Counters c;
         BCD_CUDA(cudaMemcpyAsync(&c, ws.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->stream));
         BCD_CUDA(cudaStreamSynchronize(g->stream));
+        g->last_ms_launch = 0;
+        if (timed) {
+            cudaEventElapsedTime(&g->last_ms_launch, ev0, ev1);
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+        }
         if (c.err == kDevOk) {
+            g->last = c;
             if (levels_out) *levels_out = (int)c.levels_max;
             if (edges_out) *edges_out = c.edges;
             g->last_ns_fwd = c.ns_fwd;
