@@ -252,6 +252,43 @@ typedef struct {
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);
 bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
 
+/*
+ * RV(r) for callers that cannot allocate device memory. (The paper has no
+ * counterpart: this is a deployment variant of bc_rv_compute.)
+ *
+ * Some callers may not call cudaMalloc: code running inside another
+ * framework's allocator callbacks or teardown, processes whose device memory
+ * is fully reserved by a caching allocator, and plugins that are handed a
+ * stream and caller-owned buffers but no right to allocate. This call
+ * allocates nothing. Its working memory is one file-scope device array of
+ * about 33 MB (a visited bitmap and two frontier queues sized for
+ * BC_NOALLOC_MAX_VERTICES vertices), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ *   d_roffsets[n+1], d_rcols[m]  R(G) in CSR form, device memory (for example
+ *                                from bc_graph_reverse, copied back to the
+ *                                device by the caller); weights are not used;
+ *   n                            1 .. BC_NOALLOC_MAX_VERTICES, else
+ *                                BC_E_INVALID_ARG;
+ *   r                            the query vertex;
+ *   d_out[cap]                   device buffer for RV(r), ascending, r
+ *                                excluded; nothing is written when
+ *                                cap < |RV(r)| (BC_E_BUFFER_TOO_SMALL);
+ *   *count                       host: |RV(r)|;
+ *   stream                       cudaStream_t the work is queued on; the call
+ *                                returns after it has finished.
+ *
+ * The first call on a device looks up the array's device address (and may
+ * load the module there); make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents; the
+ * call clears what must start empty. Calls that overlap on the GPU (from two
+ * threads or two streams) race on the array and must be serialised by the
+ * caller.
+ */
+#define BC_NOALLOC_MAX_VERTICES 4194304
+bc_status bc_rv_compute_noalloc(const int64_t *d_roffsets, const int32_t *d_rcols, int32_t n, int32_t r,
+                                int32_t *d_out, int64_t cap, int64_t *count, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *bc_last_error(void);
 

@@ -98,6 +98,8 @@ _SIGNATURES = {
                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "bc_set_config": (C.c_int, [C.c_void_p, C.POINTER(bc_config)]),
     "bc_get_config": (C.c_int, [C.c_void_p, C.POINTER(bc_config)]),
+    "bc_rv_compute_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                        C.POINTER(C.c_int64), C.c_void_p]),
     "bc_last_error": (C.c_char_p, []),
     "bc_version": (C.c_char_p, []),
 }
@@ -316,6 +318,22 @@ def bc_spd_probe(g: Graph, sources, targets, want_dist=True, want_sigma=True, wa
     _check(lib().bc_spd_probe(g.handle, _ptr(src), ns, _ptr(tg), nt, _ptr(dist), _ptr(sig), _ptr(dep),
                               _ptr(flags)))
     return dist, sig, (None if dep is None else dep[:, :nt]), flags
+
+
+BC_NOALLOC_MAX_VERTICES = 4194304
+
+
+def bc_rv_compute_noalloc(d_roffsets, d_rcols, n, r, d_out, cap, stream=None):
+    """RV(r) with no allocation by the library: all arguments are device
+    pointers (ints) the caller owns; returns |RV(r)| (raises BCError with
+    BC_E_BUFFER_TOO_SMALL, count unknown to the caller, if cap is short)."""
+    cnt = C.c_int64()
+    st = lib().bc_rv_compute_noalloc(C.c_void_p(d_roffsets), C.c_void_p(d_rcols), int(n), int(r),
+                                     C.c_void_p(d_out), int(cap), C.byref(cnt), C.c_void_p(stream or 0))
+    if st == BC_E_BUFFER_TOO_SMALL:
+        raise BCError(st, "%s (|RV(r)| = %d)" % (lib().bc_last_error().decode(), cnt.value))
+    _check(st)
+    return cnt.value
 
 
 def bc_version() -> str:
