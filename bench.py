@@ -290,6 +290,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """A small launch of the same traversal kernel for ncu captures: one
+    sampled query (T = args.case_T draws, seed 7) on the R-MAT 20 graph."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_08739_gb300 as bcd
+    g, qs = make_workload()
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    r = int(gg.top_inout_vertices(g, 1)[0])
+    out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
+    print(json.dumps({"case": "profile", "r": r, "T": args.case_T, "bc": out[0]["bc"], "info": info}), flush=True)
+    dg.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,11 +314,16 @@ def main():
     ap.add_argument("--tile-words", type=int, default=2)
     ap.add_argument("--cpu-sources", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="", choices=["", "profile"],
+                    help="profile: one small sampled batch (for ncu), no JSON bench line")
+    ap.add_argument("--case-T", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3
-    if args.impl == "reference":
+    if args.case == "profile":
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

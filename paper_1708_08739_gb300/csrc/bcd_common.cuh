@@ -93,6 +93,7 @@ struct TravParams {
     int64_t pcap;
     unsigned long long *lev_cnt;   // [maxlev + 2]
     unsigned long long *lev_ccnt;  // [maxlev + 2]
+    unsigned long long *lev_grab;  // [2 * (maxlev + 2)] chunk hand-out counters, forward then backward
     int64_t *lev_start;            // [maxlev + 2]
     int64_t *lev_cstart;           // [maxlev + 2]
     int32_t maxlev;
@@ -144,6 +145,7 @@ struct bcd_workspace {
     int64_t pcap = 0;
     unsigned long long *lev_cnt = nullptr;
     unsigned long long *lev_ccnt = nullptr;
+    unsigned long long *lev_grab = nullptr;
     int64_t *lev_start = nullptr;
     int64_t *lev_cstart = nullptr;
     int32_t maxlev = 0;

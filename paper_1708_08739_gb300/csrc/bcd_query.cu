@@ -205,6 +205,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.pdone);
     dev_free(ws.lev_cnt);
     dev_free(ws.lev_ccnt);
+    dev_free(ws.lev_grab);
     dev_free(ws.lev_start);
     dev_free(ws.lev_cstart);
     dev_free(ws.rvmask);
@@ -246,6 +247,7 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     ws.maxlev = (int32_t)std::min<int64_t>(n + 1, (int64_t)INT32_MAX - 4);
     BCD_TRY(dev_alloc(&ws.lev_cnt, (size_t)ws.maxlev + 2));
     BCD_TRY(dev_alloc(&ws.lev_ccnt, (size_t)ws.maxlev + 2));
+    BCD_TRY(dev_alloc(&ws.lev_grab, 2 * ((size_t)ws.maxlev + 2)));
     BCD_TRY(dev_alloc(&ws.lev_start, (size_t)ws.maxlev + 2));
     BCD_TRY(dev_alloc(&ws.lev_cstart, (size_t)ws.maxlev + 2));
     BCD_TRY(dev_alloc(&ws.rvmask, (size_t)n));

@@ -94,6 +94,28 @@ __device__ __forceinline__ bool mask_bit(const uint64_t (&m)[W], int s) {
     return (m[s >> 6] >> (s & 63)) & 1ull;
 }
 
+// Dynamic hand-out of a level's chunks to warps: lane 0 grabs `grab`
+// consecutive chunks with one atomic, so warps that drew cheap chunks take
+// more and the level ends evenly.
+struct ChunkGrabber {
+    unsigned long long *ctr;
+    long long ccnt, grab, cur, end;
+    __device__ ChunkGrabber(unsigned long long *c, long long n, long long nwarps)
+        : ctr(c), ccnt(n), grab(max(1ll, n / (nwarps * 8))), cur(0), end(0) {}
+    __device__ __forceinline__ bool next(long long &c, int lane) {
+        if (cur >= end) {
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(ctr, (unsigned long long)grab);
+            b = __shfl_sync(kFull, b, 0);
+            if ((long long)b >= ccnt) return false;
+            cur = (long long)b;
+            end = min(ccnt, (long long)b + grab);
+        }
+        c = cur++;
+        return true;
+    }
+};
+
 // Bytes of shared memory each warp stages backward gathers in.
 constexpr int kStageBytes = 4096;
 
@@ -293,7 +315,9 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
     const int nxt = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
     const int CH = p.chunk_arcs;
-    for (long long c = gwarp; c < ccnt; c += nwarps) {
+    ChunkGrabber grab(&p.lev_grab[L], ccnt, nwarps);
+    long long c;
+    while (grab.next(c, lane)) {
         const Chunk ch = load_chunk(&p.chunks[cs + c]);
         const int v = ch.v, e = ch.e;
         const long long a0 = ch.a0;
@@ -457,7 +481,9 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
     const int lane = threadIdx.x & 31;
     const int nx = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
-    for (long long c = gwarp; c < ccnt; c += nwarps) {
+    ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + L], ccnt, nwarps);
+    long long c;
+    while (grab.next(c, lane)) {
         const Chunk ch = load_chunk(&p.chunks[cs + c]);
         const int v = ch.v, e = ch.e, k = ch.k, nch = ch.nch;
         const long long a0 = ch.a0;
@@ -758,6 +784,8 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
                 for (int l = threadIdx.x; l <= Lmax + 1; l += blockDim.x) {
                     p.lev_cnt[l] = 0ull;
                     p.lev_ccnt[l] = 0ull;
+                    p.lev_grab[l] = 0ull;
+                    p.lev_grab[p.maxlev + 2 + l] = 0ull;
                 }
                 if (threadIdx.x == 0) p.ctr->pslots = 0ull;
             }
@@ -803,6 +831,7 @@ bc_status reset_dense_state(bc_graph *g) {
     BCD_CUDA(cudaMemsetAsync(ws.sigma, 0, sizeof(double) * (size_t)ws.n * 64 * ws.W, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 2 * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)ws.pcap, g->stream));
     return BC_OK;
 }
@@ -825,6 +854,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.pcap = ws.pcap;
         p.lev_cnt = ws.lev_cnt;
         p.lev_ccnt = ws.lev_ccnt;
+        p.lev_grab = ws.lev_grab;
         p.lev_start = ws.lev_start;
         p.lev_cstart = ws.lev_cstart;
         p.maxlev = ws.maxlev;
