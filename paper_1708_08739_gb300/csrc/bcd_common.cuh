@@ -52,7 +52,7 @@ struct __align__(16) Chunk {
     int32_t nch;
     int64_t a0;
     int32_t na;
-    int32_t pad;
+    int32_t pad;   // kind: 0 out-arcs, 1 in-arcs (weighted sigma pull)
 };
 
 // Traversal modes of the persistent kernel.
@@ -111,6 +111,19 @@ struct TravParams {
     double *tile_partial;    // [ntiles * 64]
     uint32_t *qflags;        // [64]
     uint64_t *srcflag;       // [W] sigma >= 2^53 seen for a source slot (this tile)
+    // weighted graphs (Dial buckets on exact distances)
+    const uint32_t *wt;      // [m] forward arc weights
+    const int64_t *roff;     // [n + 1] R(G)
+    const int32_t *rcol;     // [m]
+    const uint32_t *rwt;     // [m] weights of R(G)'s arcs
+    uint64_t *dist;          // [n * S] tentative, then final distances (UINT64_MAX unreached)
+    uint32_t *qbits;         // [n * ring / 32] bucket slots a vertex is queued in
+    int32_t *buckets;        // [ring * bcap]
+    unsigned long long *bcount;  // [ring]
+    int64_t bcap;
+    int32_t ring;            // power of two above the largest weight
+    int32_t pad2;
+    int64_t *lev_dist;       // [maxlev + 2] distance of each non-empty level
     // reach mode output
     uint64_t *rvmask;        // [n]
     int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
@@ -155,6 +168,13 @@ struct bcd_workspace {
     uint64_t *qmask = nullptr;    // [n]
     int32_t *posd = nullptr;      // [n] position of a vertex in the source union
     int32_t *hublev = nullptr;    // [n] hop distance to the hub (tile ordering key), -1 unreached
+    // weighted graphs
+    uint64_t *dist = nullptr;     // [n * 64]
+    uint32_t *qbits = nullptr;    // [n * ring / 32]
+    int32_t *buckets = nullptr;   // [ring * n]
+    unsigned long long *bcount = nullptr;  // [ring]
+    int64_t *lev_dist = nullptr;  // [maxlev + 2]
+    int32_t ring = 0;
     int32_t hub = -1;             // vertex the ordering key is measured to
     int32_t *dlist = nullptr;     // [n + 64*4] source union, padded to whole tiles
     int32_t *qlevel = nullptr;    // [256 * 64]
@@ -193,6 +213,7 @@ struct bc_graph {
     int32_t n = 0;
     int64_t m = 0;
     bool weighted = false;
+    uint32_t max_weight = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -244,6 +265,8 @@ void free_workspace(bc_graph *g);
 
 // traversal launcher (bcd_traverse.cu)
 bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out);
+bc_status launch_weighted(bc_graph *g, TravParams &p);  // bcd_wtraverse.cu
+bc_status ensure_weighted_state(bc_graph *g);
 bc_status reset_dense_state(bc_graph *g);
 
 template <typename T>

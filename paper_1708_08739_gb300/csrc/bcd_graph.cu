@@ -61,6 +61,14 @@ __global__ void check_rows(const int64_t *off, const int32_t *col, const uint32_
     }
 }
 
+__global__ void max_weight(const uint32_t *w, int64_t m, unsigned *out) {
+    unsigned mx = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        mx = max(mx, w[i]);
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
 __global__ void count_heads(const int32_t *col, int64_t m, int64_t *cnt) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
         atomicAdd((unsigned long long *)&cnt[col[i]], 1ull);
@@ -218,6 +226,19 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
                                   "bc_graph_create: a row is not strictly increasing (rows must be sorted, without repeated arcs)"));
         case kGWeight: return fail(set_error(BC_E_INVALID_GRAPH, "bc_graph_create: zero weight (weights must be positive)"));
         default: return fail(set_error(BC_E_INTERNAL, "bc_graph_create: unknown validation code"));
+    }
+
+    if (g->weighted && m) {
+        unsigned *d_mx = nullptr;
+        if ((st = dev_alloc(&d_mx, 1))) return fail(st);
+        cudaMemsetAsync(d_mx, 0, sizeof(unsigned), s);
+        max_weight<<<gblocks, tb, 0, s>>>(g->d_w, d->m, d_mx);
+        unsigned hmx = 0;
+        cudaMemcpyAsync(&hmx, d_mx, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        ce = cudaStreamSynchronize(s);
+        dev_free(d_mx);
+        if (ce != cudaSuccess) return fail(cuda_error(ce, "max weight"));
+        g->max_weight = hmx;
     }
 
     // R(G): in-degree count, exclusive scan, scatter

@@ -186,6 +186,27 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     return BC_OK;
 }
 
+bc_status ensure_weighted_state(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    if (ws.dist) return BC_OK;
+    int R = 32;
+    while ((uint32_t)R <= g->max_weight) R *= 2;
+    if (R > 4096) return set_error(BC_E_INVALID_ARG, "weighted graphs need arc weights of at most 4095");
+    ws.ring = R;
+    const size_t n = (size_t)g->n;
+    BCD_TRY(dev_alloc(&ws.dist, n * 64));
+    BCD_TRY(dev_alloc(&ws.qbits, n * (size_t)(R / 32)));
+    BCD_TRY(dev_alloc(&ws.buckets, n * (size_t)R));
+    BCD_TRY(dev_alloc(&ws.bcount, (size_t)R));
+    BCD_TRY(dev_alloc(&ws.lev_dist, (size_t)ws.maxlev + 2));
+    BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * n * 64, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.qbits, 0, sizeof(uint32_t) * n * (size_t)(R / 32), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * (size_t)R, g->stream));
+    // a weighted tile usually settles a vertex once per source
+    if (ws.hcap < 32 * (int64_t)n + 4096) BCD_TRY(alloc_history(g, 32 * (int64_t)n + 4096, ws.ccap, ws.pcap));
+    return BC_OK;
+}
+
 bc_status grow_history(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (ws.hcap >= (int64_t)INT32_MAX - 1) return set_error(BC_E_OOM, "level history exceeds 2^31 entries");
@@ -213,6 +234,11 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.qmask);
     dev_free(ws.posd);
     dev_free(ws.hublev);
+    dev_free(ws.dist);
+    dev_free(ws.qbits);
+    dev_free(ws.buckets);
+    dev_free(ws.bcount);
+    dev_free(ws.lev_dist);
     dev_free(ws.dlist);
     dev_free(ws.qlevel);
     dev_free(ws.dep);
@@ -471,7 +497,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
     const int nq = (int)qs.size();
-    const int W = g->tile_words;
+    const int W = g->weighted ? 1 : g->tile_words;
     const int S = 64 * W;
     // the ordering key's reach traversal uses the union buffer: run it first
     if (g->source_order == 1) BCD_TRY(ensure_hub_levels(g));
@@ -639,9 +665,9 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
 
 static bc_status check_graph(bc_graph *g, const char *fn) {
     if (!g) return set_error(BC_E_INVALID_ARG, std::string(fn) + ": NULL graph");
-    if (g->weighted)
-        return set_error(BC_E_INVALID_ARG, std::string(fn) + ": weighted shortest paths are not supported yet");
-    return ensure_workspace(g, g->tile_words);
+    BCD_TRY(ensure_workspace(g, g->tile_words));
+    if (g->weighted) BCD_TRY(ensure_weighted_state(g));
+    return BC_OK;
 }
 
 static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out, bc_batch_info *info) {
@@ -873,7 +899,7 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
     BCD_TRY(check_graph(g, "bc_spd_probe"));
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
-    const int W = ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
+    const int W = g->weighted ? 1 : ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
     const int S = 64 * W;
     for (int i = 0; i < nsrc; ++i) {
         if (sources[i] < 0 || sources[i] >= g->n) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: source out of range");
@@ -951,13 +977,19 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
             if (st == BC_OK) {
                 if (dist) std::fill(dist, dist + (size_t)nsrc * n, ~0ull);
                 if (sigma) std::fill(sigma, sigma + (size_t)nsrc * n, 0.0);
+                std::vector<uint64_t> wd;
+                if (g->weighted && dist) {
+                    wd.resize(n * 64);
+                    BCD_CUDA(cudaMemcpyAsync(wd.data(), ws.dist, sizeof(uint64_t) * n * 64, cudaMemcpyDeviceToHost, s));
+                    BCD_CUDA(cudaStreamSynchronize(s));
+                }
                 int64_t e = 0;
                 for (int L = 0; L < levels; ++L) {
                     for (unsigned long long k = 0; k < lc[L]; ++k, ++e) {
                         const int32_t v = hv[e];
                         for (int i = 0; i < nsrc; ++i) {
                             if ((hm[e * W + (i >> 6)] >> (i & 63)) & 1ull) {
-                                if (dist) dist[(size_t)i * n + v] = (uint64_t)L;
+                                if (dist) dist[(size_t)i * n + v] = g->weighted ? wd[(size_t)v * 64 + i] : (uint64_t)L;
                                 if (sigma) sigma[(size_t)i * n + v] = sg[(size_t)v * S + i];
                             }
                         }

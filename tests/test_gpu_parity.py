@@ -283,6 +283,75 @@ def test_invalid_graphs_rejected(bcd):
     assert out[1]["status"] == bcd.BC_E_INVALID_ARG and out[2]["status"] == bcd.BC_E_INVALID_ARG
 
 
+# ---------------------------------------------------------------- weighted
+
+@pytest.fixture(scope="module")
+def wer():
+    """ER 600 / 4,000 with weights uniform in [1, 255] (seed 3) and a copy
+    with weights in [1, 3], whose many equal-length paths make sigma > 1."""
+    g = gg.erdos_renyi(600, 4000, 21)
+    g255 = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    g3 = g.with_weights(gg.uniform_weights(g.m, 1, 3, 4))
+    return [(x, O.Graph.from_csr(x)) for x in (g255, g3)]
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_weighted_probe_dist_sigma_delta(bcd, wer, which):
+    g, og = wer[which]
+    dg = make(bcd, g)
+    srcs = np.array(sorted(set(gg.random_vertices(g.n, 30, 5).tolist())), dtype=np.int32)
+    tgts = np.array(list(dict.fromkeys(gg.random_vertices(g.n, 12, 6).tolist())), dtype=np.int32)
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, tgts)
+    for i, s in enumerate(srcs.tolist()):
+        st = O.source_state(og, s)
+        assert np.array_equal(dist[i], st["dist"]), s
+        assert np.array_equal(sig[i], st["sigma"]), s
+        for j, t in enumerate(tgts.tolist()):
+            if t != s:
+                assert close(dep[i, j], st["delta"][t]), (s, t, dep[i, j], st["delta"][t])
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_weighted_exact_and_batch(bcd, wer, which):
+    g, og = wer[which]
+    dg = make(bcd, g)
+    qs = gg.random_vertices(g.n, 12, 104).tolist()
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    for r, o in zip(qs, out):
+        want, k, _ = O.bc_exact(og, r, 0)
+        single, info = bcd.bc_exact(dg, r)
+        assert o["status"] == 0 and o["rv_size"] == k == info["rv_size"]
+        assert close(o["bc"], want) and close(single, want), (r, o["bc"], single, want)
+
+
+def test_weighted_closed_forms_and_sampling(bcd, wer):
+    wt = csr(3, [(0, 1), (0, 2), (2, 1)], [2, 1, 1])
+    dg = make(bcd, wt)
+    assert bcd.bc_exact(dg, 2)[0] == 0.5
+    path = csr(5, [(i, i + 1) for i in range(4)], [7, 1, 255, 3])
+    dg = make(bcd, path)
+    assert [bcd.bc_exact(dg, r)[0] for r in range(5)] == [0.0, 3.0, 4.0, 3.0, 0.0]
+    g, og = wer[1]
+    dg = make(bcd, g)
+    for r in (4, 77):
+        want, draws, k, _ = O.bc_approx(og, r, 600, 7, 0)
+        got, info = bcd.bc_approx_T(dg, r, 600, 7)
+        assert info["rv_size"] == k and close(got, want)
+
+
+def test_weighted_rmat_small(bcd):
+    """A small weighted R-MAT (the weighted configuration at scale 12)."""
+    g = gg.rmat(12, 8, seed=12)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    og = O.Graph.from_csr(g)
+    dg = make(bcd, g)
+    qs = gg.random_vertices(g.n, 8, 104).tolist() + gg.top_inout_vertices(g, 2).tolist()
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    for r, o in zip(qs, out):
+        want = O.bc_exact(og, r, 0)[0]
+        assert close(o["bc"], want), (r, o["bc"], want)
+
+
 def test_device_input_arrays(bcd, er1):
     torch = pytest.importorskip("torch")
     g, og = er1
