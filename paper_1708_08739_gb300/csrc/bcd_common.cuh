@@ -261,6 +261,8 @@ bc_status cuda_error(cudaError_t e, const char *what);
 // workspace management (bcd_query.cu)
 bc_status ensure_workspace(bc_graph *g, int W);
 bc_status grow_history(bc_graph *g);
+bc_status alloc_levels(bc_graph *g, int64_t maxlev);
+bc_status grow_levels(bc_graph *g);
 void free_workspace(bc_graph *g);
 
 // traversal launcher (bcd_traverse.cu)

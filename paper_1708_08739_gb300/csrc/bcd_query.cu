@@ -186,6 +186,36 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     return BC_OK;
 }
 
+// Per-level arrays of the traversal (entries, chunks, hand-out counters,
+// starts; distances for weighted graphs), sized for maxlev levels.
+bc_status alloc_levels(bc_graph *g, int64_t maxlev) {
+    bcd_workspace &ws = g->ws;
+    dev_free(ws.lev_cnt);
+    dev_free(ws.lev_ccnt);
+    dev_free(ws.lev_grab);
+    dev_free(ws.lev_start);
+    dev_free(ws.lev_cstart);
+    dev_free(ws.lev_dist);
+    ws.maxlev = (int32_t)maxlev;
+    const size_t L = (size_t)maxlev + 2;
+    BCD_TRY(dev_alloc(&ws.lev_cnt, L));
+    BCD_TRY(dev_alloc(&ws.lev_ccnt, L));
+    BCD_TRY(dev_alloc(&ws.lev_grab, 2 * L));
+    BCD_TRY(dev_alloc(&ws.lev_start, L));
+    BCD_TRY(dev_alloc(&ws.lev_cstart, L));
+    if (g->weighted) BCD_TRY(dev_alloc(&ws.lev_dist, L));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * L, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * L, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 2 * L, g->stream));
+    return BC_OK;
+}
+
+bc_status grow_levels(bc_graph *g) {
+    const int64_t cur = g->ws.maxlev;
+    if (cur >= (int64_t)INT32_MAX / 4) return set_error(BC_E_OOM, "traversal: more levels than the level arrays can hold");
+    return alloc_levels(g, std::min<int64_t>(cur * 4, (int64_t)INT32_MAX / 4));
+}
+
 bc_status ensure_weighted_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (ws.dist) return BC_OK;
@@ -198,7 +228,6 @@ bc_status ensure_weighted_state(bc_graph *g) {
     BCD_TRY(dev_alloc(&ws.qbits, n * (size_t)(R / 32)));
     BCD_TRY(dev_alloc(&ws.buckets, n * (size_t)R));
     BCD_TRY(dev_alloc(&ws.bcount, (size_t)R));
-    BCD_TRY(dev_alloc(&ws.lev_dist, (size_t)ws.maxlev + 2));
     BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * n * 64, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.qbits, 0, sizeof(uint32_t) * n * (size_t)(R / 32), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * (size_t)R, g->stream));
@@ -270,12 +299,8 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.sigma, (size_t)n * 64 * W));
     const int64_t ch = g->chunk_arcs;
     BCD_TRY(alloc_history(g, 8 * n + 4096, 8 * n + 8 * (m / ch) + 4096, 8 * (m / ch) + 4096));
-    ws.maxlev = (int32_t)std::min<int64_t>(n + 1, (int64_t)INT32_MAX - 4);
-    BCD_TRY(dev_alloc(&ws.lev_cnt, (size_t)ws.maxlev + 2));
-    BCD_TRY(dev_alloc(&ws.lev_ccnt, (size_t)ws.maxlev + 2));
-    BCD_TRY(dev_alloc(&ws.lev_grab, 2 * ((size_t)ws.maxlev + 2)));
-    BCD_TRY(dev_alloc(&ws.lev_start, (size_t)ws.maxlev + 2));
-    BCD_TRY(dev_alloc(&ws.lev_cstart, (size_t)ws.maxlev + 2));
+    BCD_TRY(alloc_levels(g, std::min<int64_t>(g->weighted ? std::max<int64_t>(n + 1, 65536) : n + 1,
+                                              (int64_t)INT32_MAX / 4)));
     BCD_TRY(dev_alloc(&ws.rvmask, (size_t)n));
     BCD_TRY(dev_alloc(&ws.need, (size_t)n));
     BCD_TRY(dev_alloc(&ws.qmask, (size_t)n));

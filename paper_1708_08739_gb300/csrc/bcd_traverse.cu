@@ -801,8 +801,11 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             return set_error(BC_E_TIMEOUT, "traversal: a grid barrier wait timed out");
         }
         if (c.err == kDevLevelOverflow) {
-            reset_dense_state(g);
-            return set_error(BC_E_INTERNAL, "traversal: level count exceeded the vertex count");
+            // more non-empty levels than the arrays hold (integer weights): grow and rerun
+            BCD_TRY(grow_levels(g));
+            BCD_TRY(reset_dense_state(g));
+            if (p.qflags) BCD_CUDA(cudaMemsetAsync(p.qflags, 0, sizeof(uint32_t) * 64, g->stream));
+            continue;
         }
         // capacity overflow: grow the level history and retry from a clean state
         BCD_TRY(grow_history(g));
