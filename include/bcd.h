@@ -47,7 +47,9 @@ typedef enum {
     BC_E_CUDA = 4,             /* a CUDA runtime call failed */
     BC_E_BUFFER_TOO_SMALL = 5, /* output capacity below the needed count */
     BC_E_TIMEOUT = 6,          /* a bounded device wait gave up */
-    BC_E_INTERNAL = 7
+    BC_E_INTERNAL = 7,
+    BC_E_BUSY = 8,             /* bc_submit: the server's queue is full; retry later */
+    BC_E_PENDING = 9           /* bc_poll: the query has not finished yet */
 } bc_status;
 
 typedef enum { BC_MEM_HOST = 0, BC_MEM_DEVICE = 1 } bc_mem_kind;
@@ -226,6 +228,58 @@ bc_status bc_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *
  */
 bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const int32_t *targets,
                        int32_t nt, uint64_t *dist, double *sigma, double *dep, uint32_t *flags);
+
+/*
+ * Serving with continuous batching (the set version of Section 4.2 applied to
+ * a stream of queries). A server owns a worker thread that runs queries on
+ * the graph; while it exists, the graph must not be used by other calls.
+ *
+ * Admission: a submitted query waits until one of max_active query slots
+ * (at most 64) is free and the number of admitted sources not yet run is
+ * below max_pending_sources (each pending source holds a slot in the device
+ * staging of the next slices; the dist/sigma/delta slabs themselves are per
+ * tile and shared). Then its source set is prepared (RV(r); Philox draws for
+ * sampled queries) and merged into the pool of pending sources: a source
+ * already pending for another query is run once for both. The worker runs
+ * the pool in slices of tiles_per_slice tiles, taking sources round-robin
+ * across the active queries, so queries that arrive while others run get
+ * their work into the next slice. Each result equals the single-query call
+ * up to fp64 summation order.
+ */
+typedef struct bc_server bc_server;
+
+typedef struct {
+    int32_t max_active;          /* query slots in flight, 1..64 (0: 64) */
+    int32_t tiles_per_slice;     /* tiles per traversal launch (0: 16) */
+    int64_t max_pending_sources; /* admission bound on pending sources (0: 2^26) */
+    int64_t max_queue;           /* bound on submitted, unadmitted queries (0: 2^20) */
+} bc_server_config;
+
+typedef struct {
+    int64_t submitted, admitted, completed;
+    int64_t slices;              /* traversal launches */
+    int64_t sources_run;
+    int64_t edges_traversed;
+    int64_t active, queued;      /* at the time of the call */
+    double busy_ms;              /* wall time of the slices */
+} bc_server_stats;
+
+/* Starts the worker. cfg may be NULL (defaults). */
+bc_status bc_server_create(bc_graph *g, const bc_server_config *cfg, bc_server **out);
+
+/* Queues a query; *ticket identifies it. BC_E_BUSY when the queue is full,
+ * BC_E_INVALID_ARG for a bad query (no ticket then). Thread-safe. */
+bc_status bc_submit(bc_server *srv, const bc_query *q, uint64_t *ticket);
+
+/* Waits up to timeout_us for the query; BC_OK fills *out (and the latency
+ * from submission to completion, if latency_ms is not NULL) and releases the
+ * ticket; BC_E_PENDING if not finished yet. Thread-safe. */
+bc_status bc_poll(bc_server *srv, uint64_t ticket, bc_result *out, double *latency_ms, int64_t timeout_us);
+
+bc_status bc_server_stats_get(bc_server *srv, bc_server_stats *stats);
+
+/* Stops the worker (unfinished queries are dropped) and frees the server. */
+void bc_server_destroy(bc_server *srv);
 
 /*
  * Tuning of the batched traversal (no effect on results beyond fp64

@@ -26,6 +26,8 @@ BC_E_CUDA = 4
 BC_E_BUFFER_TOO_SMALL = 5
 BC_E_TIMEOUT = 6
 BC_E_INTERNAL = 7
+BC_E_BUSY = 8
+BC_E_PENDING = 9
 
 BC_MEM_HOST = 0
 BC_MEM_DEVICE = 1
@@ -76,6 +78,17 @@ class bc_config(C.Structure):
                 ("source_order", C.c_int32)]
 
 
+class bc_server_config(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("tiles_per_slice", C.c_int32), ("max_pending_sources", C.c_int64),
+                ("max_queue", C.c_int64)]
+
+
+class bc_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("slices", C.c_int64), ("sources_run", C.c_int64), ("edges_traversed", C.c_int64),
+                ("active", C.c_int64), ("queued", C.c_int64), ("busy_ms", C.c_double)]
+
+
 # every symbol declared in include/bcd.h, with its ctypes signature
 _SIGNATURES = {
     "bc_graph_create": (C.c_int, [C.POINTER(bc_graph_desc), C.POINTER(C.c_void_p)]),
@@ -100,6 +113,11 @@ _SIGNATURES = {
     "bc_get_config": (C.c_int, [C.c_void_p, C.POINTER(bc_config)]),
     "bc_rv_compute_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
                                         C.POINTER(C.c_int64), C.c_void_p]),
+    "bc_server_create": (C.c_int, [C.c_void_p, C.POINTER(bc_server_config), C.POINTER(C.c_void_p)]),
+    "bc_submit": (C.c_int, [C.c_void_p, C.POINTER(bc_query), C.POINTER(C.c_uint64)]),
+    "bc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(bc_result), C.POINTER(C.c_double), C.c_int64]),
+    "bc_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(bc_server_stats)]),
+    "bc_server_destroy": (None, [C.c_void_p]),
     "bc_last_error": (C.c_char_p, []),
     "bc_version": (C.c_char_p, []),
 }
@@ -318,6 +336,48 @@ def bc_spd_probe(g: Graph, sources, targets, want_dist=True, want_sigma=True, wa
     _check(lib().bc_spd_probe(g.handle, _ptr(src), ns, _ptr(tg), nt, _ptr(dist), _ptr(sig), _ptr(dep),
                               _ptr(flags)))
     return dist, sig, (None if dep is None else dep[:, :nt]), flags
+
+
+class Server:
+    """Owning handle of a serving loop (bc_server) on a graph."""
+
+    def __init__(self, g: Graph, max_active=0, tiles_per_slice=0, max_pending_sources=0, max_queue=0):
+        cfg = bc_server_config(int(max_active), int(tiles_per_slice), int(max_pending_sources), int(max_queue))
+        h = C.c_void_p()
+        _check(lib().bc_server_create(g.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self.graph = g
+
+    def submit(self, spec) -> int:
+        q, _ = make_queries([spec])
+        t = C.c_uint64()
+        _check(lib().bc_submit(self.handle, q, C.byref(t)))
+        return t.value
+
+    def poll(self, ticket, timeout_us=0):
+        """(result dict, latency ms) or None while pending."""
+        r = bc_result()
+        lat = C.c_double()
+        st = lib().bc_poll(self.handle, C.c_uint64(ticket), C.byref(r), C.byref(lat), int(timeout_us))
+        if st == BC_E_PENDING:
+            return None
+        _check(st)
+        return ({"bc": r.bc, "status": r.status, "flags": r.flags, "rv_size": r.rv_size, "samples": r.samples},
+                lat.value)
+
+    def stats(self) -> dict:
+        s = bc_server_stats()
+        _check(lib().bc_server_stats_get(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in bc_server_stats._fields_}
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().bc_server_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 BC_NOALLOC_MAX_VERTICES = 4194304

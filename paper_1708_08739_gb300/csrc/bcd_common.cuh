@@ -268,6 +268,26 @@ void free_workspace(bc_graph *g);
 // traversal launcher (bcd_traverse.cu)
 bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out);
 bc_status launch_weighted(bc_graph *g, TravParams &p);  // bcd_wtraverse.cu
+
+// query preparation and slices for the serving loop (bcd_query.cu)
+struct PrepItem {
+    int32_t r = 0;
+    int32_t kind = 0;
+    int64_t T = 0;
+    uint64_t seed = 0;
+    int64_t rv = 0;                 // |RV(r)|
+    bool sampled = false;           // resolved: Algorithm 2
+    std::vector<int32_t> srcs;      // distinct sources (ascending)
+    std::vector<uint32_t> mult;     // draw counts (sampled), parallel to srcs
+};
+bc_status prepare_sources(bc_graph *g, std::vector<PrepItem> &items);
+bc_status set_query_bit(bc_graph *g, int32_t v, int bit, bool on);
+bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::vector<uint64_t> &needs,
+                    const std::vector<uint32_t> &mult, uint64_t exact_q, std::vector<double> &partials,
+                    uint32_t *qflags, unsigned long long *edges);
+bc_status check_graph(bc_graph *g, const char *fn);
+bc_status prepare_ordering(bc_graph *g);
+int32_t hub_level(bc_graph *g, int32_t v);
 bc_status ensure_weighted_state(bc_graph *g);
 bc_status reset_dense_state(bc_graph *g);
 

@@ -391,7 +391,7 @@ static unsigned grid_for(const bc_graph *g, int64_t work, int threads) {
 }
 
 // RV for up to 64 distinct roots: rvmask[v] bit sl <=> v in RV(roots[sl]).
-static bc_status reach_roots(bc_graph *g, const std::vector<int32_t> &roots, std::vector<int64_t> &sizes) {
+bc_status reach_roots(bc_graph *g, const std::vector<int32_t> &roots, std::vector<int64_t> &sizes) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
     const int nr = (int)roots.size();
@@ -430,7 +430,7 @@ static bc_status reach_roots(bc_graph *g, const std::vector<int32_t> &roots, std
 }
 
 // Ascending RV lists of the given slots into ws.rvlists; offsets returned.
-static bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::vector<int64_t> &sizes,
+bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::vector<int64_t> &sizes,
                                 std::vector<int64_t> &offs) {
     bcd_workspace &ws = g->ws;
     int64_t total = 0;
@@ -688,7 +688,177 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     return BC_OK;
 }
 
-static bc_status check_graph(bc_graph *g, const char *fn) {
+// ---------------------------------------------------------------------------
+// helpers for the serving loop (bcd_server.cu)
+// ---------------------------------------------------------------------------
+
+bc_status prepare_sources(bc_graph *g, std::vector<PrepItem> &items) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    std::vector<int32_t> roots;
+    std::vector<int> slot_of(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        auto it = std::find(roots.begin(), roots.end(), items[i].r);
+        slot_of[i] = (int)(it - roots.begin());
+        if (it == roots.end()) roots.push_back(items[i].r);
+    }
+    if (roots.size() > 64) return set_error(BC_E_INTERNAL, "prepare_sources: more than 64 roots");
+    std::vector<int64_t> sizes;
+    BCD_TRY(reach_roots(g, roots, sizes));
+    std::vector<int> slots;
+    for (size_t sl = 0; sl < roots.size(); ++sl)
+        if (sizes[sl] > 0) slots.push_back((int)sl);
+    std::vector<int64_t> offs;
+    int64_t total = 0;
+    for (int sl : slots) total += sizes[sl];
+    std::vector<int32_t> lists((size_t)std::max<int64_t>(total, 1));
+    if (!slots.empty()) {
+        BCD_TRY(build_rv_lists(g, slots, sizes, offs));
+        BCD_CUDA(cudaMemcpyAsync(lists.data(), ws.rvlists, sizeof(int32_t) * (size_t)total, cudaMemcpyDeviceToHost, s));
+    }
+    // draws of the sampled items
+    std::vector<DrawSpec> specs;
+    int64_t ndraws = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        PrepItem &it = items[i];
+        it.rv = sizes[slot_of[i]];
+        it.sampled = it.kind == BC_QUERY_APPROX || it.kind == BC_QUERY_APPROX_T ||
+                     (it.kind == BC_QUERY_HYBRID && it.rv > it.T);
+        if (it.sampled && it.rv > 0) {
+            DrawSpec d;
+            d.first = ndraws;
+            d.T = it.T;
+            d.list_off = offs[slot_of[i]];
+            d.k = it.rv;
+            d.seed = it.seed;
+            d.bit = 0;
+            d.pad = 0;
+            specs.push_back(d);
+            ndraws += it.T;
+        }
+    }
+    std::vector<int32_t> draws((size_t)std::max<int64_t>(ndraws, 1));
+    if (!specs.empty()) {
+        BCD_TRY(ensure_buf(&ws.draws, &ws.draws_cap, ndraws + 1));
+        // specs go up in groups of 64 (the staging buffer holds 64)
+        for (size_t b = 0; b < specs.size(); b += 64) {
+            const size_t nb = std::min<size_t>(64, specs.size() - b);
+            DrawSpec *d_specs = (DrawSpec *)(ws.small + kSmallSpecs);
+            BCD_CUDA(cudaMemcpyAsync(d_specs, specs.data() + b, sizeof(DrawSpec) * nb, cudaMemcpyHostToDevice, s));
+            int64_t maxT = 0;
+            for (size_t k = b; k < b + nb; ++k) maxT = std::max(maxT, specs[k].T);
+            dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((maxT + 255) / 256, 4096)), (unsigned)nb);
+            draw_kernel<<<grid, 256, 0, s>>>(d_specs, (int)nb, ws.rvlists, ws.draws, nullptr);
+            BCD_CUDA(cudaStreamSynchronize(s));
+            g->launches += 1;
+        }
+        BCD_CUDA(cudaMemcpyAsync(draws.data(), ws.draws, sizeof(int32_t) * (size_t)ndraws, cudaMemcpyDeviceToHost, s));
+    }
+    BCD_CUDA(cudaStreamSynchronize(s));
+    BCD_CUDA(cudaGetLastError());
+    size_t si = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        PrepItem &it = items[i];
+        it.srcs.clear();
+        it.mult.clear();
+        if (it.rv == 0) continue;
+        if (!it.sampled) {
+            const int32_t *b = lists.data() + offs[slot_of[i]];
+            it.srcs.assign(b, b + it.rv);
+        } else {
+            const DrawSpec &d = specs[si++];
+            std::vector<int32_t> dv(draws.begin() + d.first, draws.begin() + d.first + d.T);
+            std::sort(dv.begin(), dv.end());
+            for (size_t k = 0; k < dv.size();) {
+                size_t j = k;
+                while (j < dv.size() && dv[j] == dv[k]) ++j;
+                it.srcs.push_back(dv[k]);
+                it.mult.push_back((uint32_t)(j - k));
+                k = j;
+            }
+        }
+    }
+    return BC_OK;
+}
+
+bc_status set_query_bit(bc_graph *g, int32_t v, int bit, bool on) {
+    VBit b{v, bit};
+    VBit *d = (VBit *)(g->ws.small + kSmallBits2);
+    BCD_CUDA(cudaMemcpyAsync(d, &b, sizeof(VBit), cudaMemcpyHostToDevice, g->stream));
+    set_bits<<<1, 32, 0, g->stream>>>(g->ws.qmask, d, 1, on ? 0 : 1);
+    BCD_CUDA(cudaStreamSynchronize(g->stream));
+    g->launches += 1;
+    return BC_OK;
+}
+
+__global__ void scatter_need(const int32_t *v, const uint64_t *mask, int64_t cnt, uint64_t *need) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (long long)gridDim.x * blockDim.x)
+        need[v[i]] = mask[i];
+}
+
+bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::vector<uint64_t> &needs,
+                    const std::vector<uint32_t> &mult, uint64_t exact_q, std::vector<double> &partials,
+                    uint32_t *qflags, unsigned long long *edges) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int S = 64 * (g->weighted ? 1 : g->tile_words);
+    const int64_t ntiles = (int64_t)srcs.size() / S;
+    if (ntiles * S != (int64_t)srcs.size() || ntiles == 0) return set_error(BC_E_INTERNAL, "run_slice: ragged slice");
+    std::vector<int32_t> vs;
+    std::vector<uint64_t> ms;
+    for (size_t i = 0; i < srcs.size(); ++i)
+        if (srcs[i] >= 0) {
+            vs.push_back(srcs[i]);
+            ms.push_back(needs[i]);
+        }
+    BCD_CUDA(cudaMemcpyAsync(ws.dlist, srcs.data(), sizeof(int32_t) * srcs.size(), cudaMemcpyHostToDevice, s));
+    BCD_TRY(ensure_buf(&ws.draws, &ws.draws_cap, (int64_t)vs.size() * 3 + 4));
+    int32_t *d_v = ws.draws;
+    uint64_t *d_m = (uint64_t *)(ws.draws + ((vs.size() + 3) & ~(size_t)1));
+    BCD_CUDA(cudaMemcpyAsync(d_v, vs.data(), sizeof(int32_t) * vs.size(), cudaMemcpyHostToDevice, s));
+    BCD_CUDA(cudaMemcpyAsync(d_m, ms.data(), sizeof(uint64_t) * ms.size(), cudaMemcpyHostToDevice, s));
+    scatter_need<<<grid_for(g, (int64_t)vs.size(), 256), 256, 0, s>>>(d_v, d_m, (int64_t)vs.size(), ws.need);
+    const bool any_mult = !mult.empty();
+    if (any_mult) {
+        BCD_TRY(ensure_buf(&ws.mult, &ws.mult_cap, (int64_t)mult.size()));
+        BCD_CUDA(cudaMemcpyAsync(ws.mult, mult.data(), sizeof(uint32_t) * mult.size(), cudaMemcpyHostToDevice, s));
+    }
+    BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, ntiles * 64));
+    BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeSpd;
+    p.off = g->d_off;
+    p.col = g->d_col;
+    p.srcs = ws.dlist;
+    p.ntiles = ntiles;
+    p.qmask = ws.qmask;
+    p.need = ws.need;
+    p.exact_q = exact_q;
+    p.mult = any_mult ? ws.mult : nullptr;
+    p.qlevel = ws.qlevel;
+    p.dep = ws.dep;
+    p.tile_partial = ws.tile_partial;
+    p.qflags = ws.qflags;
+    p.srcflag = ws.srcflag;
+    g->launches += 1;
+    BCD_TRY(run_traversal(g, g->weighted ? 1 : g->tile_words, p, nullptr, edges));
+    partials.resize((size_t)ntiles * 64);
+    BCD_CUDA(cudaMemcpyAsync(partials.data(), ws.tile_partial, sizeof(double) * partials.size(), cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaMemcpyAsync(qflags, ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    BCD_CUDA(cudaStreamSynchronize(s));
+    return BC_OK;
+}
+
+int32_t hub_level(bc_graph *g, int32_t v) {
+    if ((int64_t)g->h_hublev.size() != g->n) return 0;
+    const int32_t l = g->h_hublev[v];
+    return l < 0 ? 0x7fffffff : l;
+}
+
+bc_status prepare_ordering(bc_graph *g) { return g->source_order == 1 ? ensure_hub_levels(g) : BC_OK; }
+
+bc_status check_graph(bc_graph *g, const char *fn) {
     if (!g) return set_error(BC_E_INVALID_ARG, std::string(fn) + ": NULL graph");
     BCD_TRY(ensure_workspace(g, g->tile_words));
     if (g->weighted) BCD_TRY(ensure_weighted_state(g));
