@@ -45,7 +45,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # Global loads are cached in L2 only (-dlcm=cg): the persistent kernels
+    # re-read data that other SMs wrote before a grid barrier, and L1 is not
+    # coherent across SMs.
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-dlcm=cg",
+                     "-I", INCLUDE, "-I", CSRC]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
