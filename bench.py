@@ -134,6 +134,22 @@ def oracle_sample(og, D, qs, n_sources, threads, seed=7):
     return time.time() - t, int(srcs.shape[0])
 
 
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest value over all ranks (the job's step time); the value
+    itself when not distributed."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ms, world):
+    """Whole-job throughput: units of all ranks per second of the slowest."""
+    return world * units_per_rank / (ms / 1000.0)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -206,13 +222,9 @@ def run_gpu(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist if world > 1 else None)
     nq = len(qs)
-    qps = world * nq / (ms / 1000.0)
+    qps = job_rate(nq, ms, world)
     edges = float(np.mean([i["edges_traversed"] for i in infos]))
     gteps = world * edges / (ms / 1000.0) / 1e9
     trav_ms = float(np.mean([i["ms_traversal"] for i in infos]))
@@ -236,11 +248,7 @@ def run_gpu(args):
     out_e, info_e = bcd.bc_batch(ge, specs)
     ge.close()
     barrier()
-    e2e_s = time.time() - t
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.time() - t, dist if world > 1 else None)
     h2d = g.offsets.nbytes + g.cols.nbytes + nq * 40
     d2h = nq * 32
 
@@ -276,7 +284,7 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "trav_kernel (batched SPD + dependency traversal)",
                          "algorithmic_bytes": algo_bytes},
-            "e2e": {"value": world * nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(nq, 1000.0 * e2e_s, world), "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
@@ -288,6 +296,108 @@ def run_gpu(args):
     dg.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def serve_workload(bcd, dg, g, nq, rv_max, seed=106):
+    """Zipf(1.1) query vertices over permuted ids, re-drawn until
+    1 <= |RV(r)| <= rv_max; alternately exact and sampled (eps 0.02,
+    delta 0.1, Philox seed 7)."""
+    sizes = {}
+    out = []
+    draws = 0
+    rnd = 0
+    while len(out) < nq and rnd < 64:
+        cand = gg.zipf_vertices(g.n, 4 * nq, 1.1, seed + rnd)
+        rnd += 1
+        for r in cand.tolist():
+            draws += 1
+            if r not in sizes:
+                sizes[r] = 0 if g.offsets[r + 1] == g.offsets[r] else bcd.bc_rv_compute(dg, r).shape[0]
+            if 1 <= sizes[r] <= rv_max:
+                out.append(r)
+                if len(out) == nq:
+                    break
+    specs = []
+    for i, r in enumerate(out):
+        if i % 2 == 0:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_EXACT})
+        else:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX, "eps": 0.02, "delta": 0.1, "seed": 7})
+    return specs, draws, [sizes[r] for r in out]
+
+
+def serve_run(bcd, srv, specs, rate=None, seed=11):
+    """Submits every query (all at once, or with Poisson gaps of mean
+    1/rate), waits for all; returns (wall seconds, latencies ms)."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=len(specs)) if rate else np.zeros(len(specs))
+    tickets = []
+    t0 = time.time()
+    next_t = t0
+    pending = {}
+    lat = []
+    for s, gap in zip(specs, gaps):
+        next_t += gap
+        while time.time() < next_t:
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    lat.append(r[1])
+                    del pending[t]
+            time.sleep(0.0005)
+        t = srv.submit(s)
+        pending[t] = True
+    while pending:
+        for t in list(pending):
+            r = srv.poll(t, timeout_us=2000)
+            if r is not None:
+                lat.append(r[1])
+                del pending[t]
+    return time.time() - t0, lat
+
+
+def run_serve(args):
+    """Serving: continuous batching under Poisson arrivals, p50/p99."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_08739_gb300 as bcd
+    t0 = time.time()
+    g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
+    log("serve graph: n=%d m=%d in %.1fs" % (g.n, g.m, time.time() - t0))
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    specs, draws, rvs = serve_workload(bcd, dg, g, args.serve_queries, args.serve_rv_max)
+    log("serve queries: %d (from %d draws), |RV| %d..%d" % (len(specs), draws, min(rvs), max(rvs)))
+    srv = bcd.Server(dg)
+    serve_run(bcd, srv, specs[: max(4, len(specs) // 8)])  # warm-up
+    wall, lat = serve_run(bcd, srv, specs)
+    sat = len(specs) / wall
+    runs = {"closed_loop": {"queries_per_s": sat, "p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99))}}
+    for f in (0.5, 0.8, 1.0):
+        w, l = serve_run(bcd, srv, specs, rate=f * sat, seed=int(100 * f))
+        runs["poisson_%.1fx" % f] = {"arrival_rate": f * sat, "queries_per_s": len(specs) / w,
+                                      "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
+    st = srv.stats()
+    srv.close()
+    # one query at a time, same queries
+    t = time.time()
+    for s in specs:
+        if s["kind"] == bcd.BC_QUERY_EXACT:
+            bcd.bc_exact(dg, s["r"])
+        else:
+            bcd.bc_approx(dg, s["r"], s["eps"], s["delta"], s["seed"])
+    single = len(specs) / (time.time() - t)
+    line = {"metric": METRIC, "value": sat, "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1000.0 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serve_rmat22_recip30_zipf", "n": g.n, "m": g.m, "queries": len(specs),
+                       "rv_range": [min(rvs), max(rvs)], "mix": "alternate exact / sampled eps 0.02 delta 0.1"},
+            "serving": runs, "one_at_a_time_queries_per_s": single, "server_stats": st}
+    print(json.dumps(line), flush=True)
+    dg.close()
 
 
 def run_profile_case(args):
@@ -317,11 +427,16 @@ def main():
     ap.add_argument("--case", default="", choices=["", "profile"],
                     help="profile: one small sampled batch (for ncu), no JSON bench line")
     ap.add_argument("--case-T", type=int, default=512)
+    ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
+    ap.add_argument("--serve-queries", type=int, default=256)
+    ap.add_argument("--serve-rv-max", type=int, default=100000)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 steps")
         args.warmup = 3
-    if args.case == "profile":
+    if args.serve:
+        run_serve(args)
+    elif args.case == "profile":
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

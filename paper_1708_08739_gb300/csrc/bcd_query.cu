@@ -1158,9 +1158,11 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
             cudaMemcpyAsync(sf.data(), ws.srcflag, sizeof(uint64_t) * W, cudaMemcpyDeviceToHost, s);
             cudaError_t ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) st = cuda_error(ce, "probe export");
+            // every recorded level (a weighted level can be empty: all its queued
+            // vertices were superseded by shorter distances)
             int64_t total = 0;
-            int levels = 0;
-            while (levels < ws.maxlev + 1 && lc[levels] > 0) total += (int64_t)lc[levels++];
+            const int levels = (int)std::min<unsigned long long>(g->last.levels_max + 1, (unsigned long long)ws.maxlev + 1);
+            for (int L = 0; L < levels; ++L) total += (int64_t)lc[L];
             std::vector<int32_t> hv(std::max<int64_t>(total, 1));
             std::vector<uint64_t> hm(std::max<int64_t>(total, 1) * W);
             if (st == BC_OK && total > 0) {

@@ -1,0 +1,108 @@
+"""Serving loop (continuous batching): every result is the same alone and in
+the mix, within the parity tolerance, including queries submitted while
+others are running; sampled queries keep their own draw streams."""
+import time
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+
+
+def close(a, b):
+    return abs(a - b) <= REL * max(1.0, abs(b))
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import paper_1708_08739_gb300 as bcd
+    g = gg.rmat(13, 8, seed=13)
+    og = O.Graph.from_csr(g)
+    rng = np.random.default_rng(3)
+    rs = gg.zipf_vertices(g.n, 60, 1.1, 55).tolist() + gg.top_inout_vertices(g, 3).tolist()
+    specs = []
+    for i, r in enumerate(rs):
+        k = i % 3
+        if k == 0:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_EXACT})
+        elif k == 1:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 400, "seed": int(rng.integers(1, 1000))})
+        else:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX, "eps": 0.1, "delta": 0.1, "seed": 7})
+    return bcd, g, og, specs
+
+
+def alone(bcd, dg, s):
+    if s["kind"] == bcd.BC_QUERY_EXACT:
+        return bcd.bc_exact(dg, s["r"])[0]
+    if s["kind"] == bcd.BC_QUERY_APPROX_T:
+        return bcd.bc_approx_T(dg, s["r"], s["T"], s["seed"])[0]
+    return bcd.bc_approx(dg, s["r"], s["eps"], s["delta"], s["seed"])[0]
+
+
+def test_server_mix_equals_alone(setup):
+    bcd, g, og, specs = setup
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    want = [alone(bcd, dg, s) for s in specs]
+    srv = bcd.Server(dg, tiles_per_slice=2)
+    # a first wave, then the rest while the first is running
+    tickets = [srv.submit(s) for s in specs[:20]]
+    time.sleep(0.05)
+    tickets += [srv.submit(s) for s in specs[20:]]
+    got = [None] * len(specs)
+    lat = [None] * len(specs)
+    deadline = time.time() + 300
+    while any(x is None for x in got) and time.time() < deadline:
+        for i, t in enumerate(tickets):
+            if got[i] is None:
+                r = srv.poll(t, timeout_us=1000)
+                if r is not None:
+                    got[i], lat[i] = r
+    st = srv.stats()
+    srv.close()
+    assert all(x is not None for x in got)
+    for s, gres, w in zip(specs, got, want):
+        assert gres["status"] == 0
+        assert close(gres["bc"], w), (s, gres["bc"], w)
+    assert st["completed"] == len(specs) and st["slices"] > 0
+    assert all(x >= 0.0 for x in lat)
+    # spot checks against the oracle
+    for s, gres in list(zip(specs, got))[:6]:
+        if s["kind"] == bcd.BC_QUERY_EXACT:
+            assert close(gres["bc"], O.bc_exact(og, s["r"], 0)[0])
+        elif s["kind"] == bcd.BC_QUERY_APPROX_T:
+            assert close(gres["bc"], O.bc_approx(og, s["r"], s["T"], s["seed"], 0)[0])
+
+
+def test_server_rejects_and_drains(setup):
+    bcd, g, og, specs = setup
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    srv = bcd.Server(dg, max_active=4, tiles_per_slice=1, max_queue=8)
+    with pytest.raises(bcd.BCError):
+        srv.submit({"r": g.n + 5})
+    with pytest.raises(bcd.BCError):
+        srv.submit({"r": 1, "kind": bcd.BC_QUERY_APPROX, "eps": 0.0, "delta": 0.1})
+    ts = []
+    busy = 0
+    for s in specs[:30]:
+        try:
+            ts.append((s, srv.submit(s)))
+        except bcd.BCError as e:
+            assert e.status == bcd.BC_E_BUSY
+            busy += 1
+    results = []
+    for s, t in ts:
+        r = None
+        while r is None:
+            r = srv.poll(t, timeout_us=100000)
+        assert r[0]["status"] == 0
+        results.append((s, r[0]["bc"]))
+    srv.close()
+    assert len(ts) + busy == 30
+    for s, bc in results:  # the graph is free again once the server is closed
+        assert close(bc, alone(bcd, dg, s))
