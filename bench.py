@@ -299,21 +299,24 @@ def run_gpu(args):
 
 
 def serve_workload(bcd, dg, g, nq, rv_max, seed=106):
-    """Zipf(1.1) query vertices over permuted ids, re-drawn until
-    1 <= |RV(r)| <= rv_max; alternately exact and sampled (eps 0.02,
-    delta 0.1, Philox seed 7)."""
+    """Zipf(1.1) query vertices over permuted ids, alternately exact and
+    sampled (eps 0.02, delta 0.1, Philox seed 7). Exact queries are re-drawn
+    until 1 <= |RV(r)| <= rv_max; sampled ones until |RV(r)| >= 1 (on this
+    graph |RV| is either tiny or the whole giant in-component, which only
+    sampling serves)."""
     sizes = {}
     out = []
     draws = 0
     rnd = 0
-    while len(out) < nq and rnd < 64:
+    while len(out) < nq and rnd < 256:
         cand = gg.zipf_vertices(g.n, 4 * nq, 1.1, seed + rnd)
         rnd += 1
         for r in cand.tolist():
             draws += 1
             if r not in sizes:
                 sizes[r] = 0 if g.offsets[r + 1] == g.offsets[r] else bcd.bc_rv_compute(dg, r).shape[0]
-            if 1 <= sizes[r] <= rv_max:
+            exact = len(out) % 2 == 0
+            if (exact and 1 <= sizes[r] <= rv_max) or (not exact and sizes[r] >= 1):
                 out.append(r)
                 if len(out) == nq:
                     break
@@ -394,7 +397,9 @@ def run_serve(args):
             "ms_per_step": 1000.0 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "serve_rmat22_recip30_zipf", "n": g.n, "m": g.m, "queries": len(specs),
-                       "rv_range": [min(rvs), max(rvs)], "mix": "alternate exact / sampled eps 0.02 delta 0.1"},
+                       "rv_exact_range": [min(rvs[0::2]), max(rvs[0::2])],
+                       "rv_sampled_range": [min(rvs[1::2]), max(rvs[1::2])] if len(rvs) > 1 else None,
+                       "mix": "alternate exact (|RV| <= %d) / sampled eps 0.02 delta 0.1 seed 7" % args.serve_rv_max},
             "serving": runs, "one_at_a_time_queries_per_s": single, "server_stats": st}
     print(json.dumps(line), flush=True)
     dg.close()

@@ -293,7 +293,9 @@ void bc_server_destroy(bc_server *srv);
  *   source_order   how the union of sources is cut into tiles: 1 (default)
  *                  groups sources by their hop distance to the vertex of
  *                  largest in-degree x out-degree, so that a tile's BFS
- *                  levels line up; 2 keeps ascending vertex ids.
+ *                  levels line up; 2 keeps ascending vertex ids;
+ *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2
+ *                  trades register spills for occupancy).
  * Zero fields keep their current value.
  */
 typedef struct {
@@ -301,6 +303,8 @@ typedef struct {
     int32_t chunk_arcs;
     int32_t block_threads;
     int32_t source_order;
+    int32_t blocks_per_sm;
+    int32_t reserved[3];
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);

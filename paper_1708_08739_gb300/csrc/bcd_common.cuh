@@ -229,6 +229,7 @@ struct bc_graph {
     int tile_words = 1;           // W of the SPD kernel
     int chunk_arcs = 128;
     int source_order = 1;         // 1: tiles ordered by distance to the hub, 0: by vertex id
+    int blocks_per_sm = 1;        // resident blocks per SM of the 256-source kernel (1 or 2)
     int block_threads = 512;
     bcd_workspace ws;
     int64_t launches = 0;

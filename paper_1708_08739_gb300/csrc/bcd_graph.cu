@@ -134,6 +134,9 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->source_order && c->source_order != 1 && c->source_order != 2)
         return set_error(BC_E_INVALID_ARG, "bc_set_config: source_order must be 1 or 2");
     if (c->source_order) g->source_order = c->source_order == 1 ? 1 : 0;
+    if (c->blocks_per_sm && c->blocks_per_sm != 1 && c->blocks_per_sm != 2)
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: blocks_per_sm must be 1 or 2");
+    if (c->blocks_per_sm) g->blocks_per_sm = c->blocks_per_sm;
     if (c->tile_words) g->tile_words = c->tile_words;
     if (c->chunk_arcs) g->chunk_arcs = c->chunk_arcs;
     if (c->block_threads) g->block_threads = c->block_threads;
@@ -146,6 +149,8 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->chunk_arcs = g->chunk_arcs;
     c->block_threads = g->block_threads;
     c->source_order = g->source_order == 1 ? 1 : 2;
+    c->blocks_per_sm = g->blocks_per_sm;
+    c->reserved[0] = c->reserved[1] = c->reserved[2] = 0;
     return BC_OK;
 }
 

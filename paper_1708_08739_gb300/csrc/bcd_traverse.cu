@@ -461,13 +461,8 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
     }
 }
 
-template <int W>
-struct KernelShape {
-    static constexpr int kMinBlocks = W >= 4 ? 1 : 2;
-};
-
-template <int W, int MODE>
-__global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(TravParams p) {
+template <int W, int MODE, int MINB>
+__global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
     constexpr int S = 64 * W;
     extern __shared__ __align__(16) double s_stage_all[];
     const int lane = threadIdx.x & 31;
@@ -678,9 +673,9 @@ __global__ void __launch_bounds__(512, KernelShape<W>::kMinBlocks) trav_kernel(T
     }
 }
 
-template <int W, int MODE>
+template <int W, int MODE, int MINB>
 bc_status launch(bc_graph *g, TravParams &p) {
-    auto kern = trav_kernel<W, MODE>;
+    auto kern = trav_kernel<W, MODE, MINB>;
     const int threads = g->block_threads;
     const size_t smem = (size_t)(threads / 32) * kStageBytes;
     BCD_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -747,7 +742,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         if (timed) cudaEventRecord(ev0, g->stream);
         if (p.mode == kModeReach) {
             if (W != 1) return set_error(BC_E_INTERNAL, "reach traversal runs with one mask word");
-            st = launch<1, kModeReach>(g, p);
+            st = launch<1, kModeReach, 2>(g, p);
         } else if (g->weighted) {
             p.wt = g->d_w;
             p.roff = g->d_roff;
@@ -762,11 +757,11 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             p.lev_dist = ws.lev_dist;
             st = launch_weighted(g, p);
         } else if (W == 1) {
-            st = launch<1, kModeSpd>(g, p);
+            st = launch<1, kModeSpd, 2>(g, p);
         } else if (W == 2) {
-            st = launch<2, kModeSpd>(g, p);
+            st = launch<2, kModeSpd, 2>(g, p);
         } else if (W == 4) {
-            st = launch<4, kModeSpd>(g, p);
+            st = g->blocks_per_sm == 2 ? launch<4, kModeSpd, 2>(g, p) : launch<4, kModeSpd, 1>(g, p);
         } else {
             return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
         }
