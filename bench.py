@@ -45,10 +45,27 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def make_workload():
-    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
-    qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
-    return g, qs
+WORKLOADS = {
+    "rmat20_ef16_exact64": "R-MAT scale 20, edge factor 16, a/b/c/d 0.57/0.19/0.19/0.05, seed 20, loops and "
+                           "repeats removed, unweighted; 64 exact queries: 32 uniform (seed 103) + 32 top "
+                           "in-degree x out-degree",
+    "rmat22_ef8_recip30_sampled64": "R-MAT scale 22, edge factor 8, seed 22, 30% of arcs also reversed (seed 22), "
+                                    "repeats removed; 64 uniform queries (seed 105), A-BCD eps 0.01 delta 0.1 "
+                                    "(T = 14,979) Philox seed 7",
+}
+
+
+def make_workload(name=WORKLOAD):
+    """(graph, query vertices, query specs as dicts for the binding)."""
+    if name == "rmat20_ef16_exact64":
+        g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
+        qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
+        return g, qs, [{"r": r} for r in qs]
+    if name == "rmat22_ef8_recip30_sampled64":
+        g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
+        qs = [int(x) for x in gg.random_vertices(g.n, 64, 105)]
+        return g, qs, [{"r": r, "kind": 1, "eps": 0.01, "delta": 0.1, "seed": 7} for r in qs]
+    raise ValueError(name)
 
 
 def peaks():
@@ -110,15 +127,24 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_union(g, qs):
-    """The union D of RV(r) over the batch's queries, by the oracle."""
+def oracle_union(g, qs, specs=None):
+    """The union D of the batch's source sets, by the oracle: RV(r) for
+    exact queries, the Philox draws for sampled ones."""
     import oracle as O
     og = O.Graph.from_csr(g)
     union = set()
     outd = g.out_degree()
-    for r in sorted(set(qs)):
-        if outd[r] > 0:
-            union.update(O.rv(og, r).tolist())
+    for i, r in enumerate(qs):
+        if outd[r] == 0:
+            continue
+        rvl = O.rv(og, r)
+        spec = specs[i] if specs else {"r": r}
+        if spec.get("kind", 0) == 0:
+            union.update(rvl.tolist())
+        elif rvl.shape[0] > 0:
+            T = O.samples_for(spec["eps"], spec["delta"])
+            k = rvl.shape[0]
+            union.update(int(rvl[O.sample_index(spec["seed"], t, k)]) for t in range(T))
     return og, np.array(sorted(union), dtype=np.int32)
 
 
@@ -156,10 +182,10 @@ def run_reference(args):
         return
     from oracle import build as ob
     ob.build()
-    g, qs = make_workload()
+    g, qs, specs = make_workload(args.workload)
     threads = os.cpu_count() or 1
     per_step = 64
-    og, D = oracle_union(g, qs)
+    og, D = oracle_union(g, qs, specs)
     nd = int(D.shape[0])
     times = []
     for i in range(args.warmup + args.steps):
@@ -171,7 +197,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(qs) / qps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "queries": len(qs), "sources_in_union": nd},
+            "data": "synthetic", "config": {"workload": args.workload, "queries": len(qs), "sources_in_union": nd},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
                              "sample": "%d of the %d union sources per step, all 64 queries; queries/s = 64 / "
                                        "(seconds per source x union size)" % (per_step, nd)},
@@ -193,12 +219,26 @@ def run_gpu(args):
     import paper_1708_08739_gb300 as bcd
 
     t0 = time.time()
-    g, qs = make_workload()
+    g, qs, specs = make_workload(args.workload)
     log("workload built in %.1fs: n=%d m=%d" % (time.time() - t0, g.n, g.m))
+    # the oracle's CPU baseline runs on the host cores meanwhile (one core is
+    # left to the thread that drives the GPU)
+    cpu_box = {}
+    cpu_thread = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import threading
+
+        def cpu_job():
+            threads = max(1, (os.cpu_count() or 2) - 1)
+            og, D = oracle_union(g, qs, specs)
+            el, ns = oracle_sample(og, D, qs, args.cpu_sources, threads)
+            cpu_box.update(el=el, ns=ns, nd=int(D.shape[0]), threads=threads)
+
+        cpu_thread = threading.Thread(target=cpu_job, daemon=True)
+        cpu_thread.start()
     stream = torch.cuda.Stream()
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, stream=stream.cuda_stream)
     bcd.bc_set_config(dg, tile_words=args.tile_words)
-    specs = [{"r": r} for r in qs]
 
     def barrier():
         torch.cuda.synchronize()
@@ -253,24 +293,20 @@ def run_gpu(args):
     d2h = nq * 32
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        og, D = oracle_union(g, qs)
-        nd = int(D.shape[0])
-        el, ns = oracle_sample(og, D, qs, args.cpu_sources, threads)
-        t_src = el / ns
-        cpu = {"value": nq / (t_src * nd), "unit": "queries/s", "cores": threads, "kind": "oracle",
+    if cpu_thread is not None:
+        cpu_thread.join()
+        t_src = cpu_box["el"] / cpu_box["ns"]
+        nd = cpu_box["nd"]
+        cpu = {"value": nq / (t_src * nd), "unit": "queries/s", "cores": cpu_box["threads"], "kind": "oracle",
                "sample": "%d of the %d union sources, delta for all 64 queries; queries/s = 64 / "
-                         "(seconds per source x union size)" % (ns, nd)}
+                         "(seconds per source x union size)" % (cpu_box["ns"], nd)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": "R-MAT scale 20, edge factor 16, a/b/c/d 0.57/0.19/0.19/0.05, "
-                                                  "seed 20, loops and repeats removed, unweighted",
+            "config": {"workload": args.workload, "recipe": WORKLOADS[args.workload],
                        "n": g.n, "m": g.m, "queries": nq,
-                       "query_mix": "32 uniform (seed 103) + 32 top in-degree x out-degree, exact",
                        "tile_words": args.tile_words, "sources_in_union": int(infos[-1]["sources_run"]),
                        "l2": "not flushed: working set (sigma slab, graph, level history) well above L2",
                        "parallelism": "replicas: each rank solves its own batch"},
@@ -411,7 +447,7 @@ def run_profile_case(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1708_08739_gb300 as bcd
-    g, qs = make_workload()
+    g, qs, _ = make_workload()
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
     bcd.bc_set_config(dg, tile_words=args.tile_words)
     r = int(gg.top_inout_vertices(g, 1)[0])
@@ -431,6 +467,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="", choices=["", "profile"],
                     help="profile: one small sampled batch (for ncu), no JSON bench line")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--case-T", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
     ap.add_argument("--serve-queries", type=int, default=256)

@@ -289,19 +289,33 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
             }
             warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
             if (MODE == kModeSpd) {
+                // two tight heads per step: their shuffles and atomics overlap
                 unsigned bal = __ballot_sync(kFull, any);
                 while (bal) {
-                    const int i = __ffs(bal) - 1;
+                    const int i0 = __ffs(bal) - 1;
                     bal &= bal - 1;
-                    const int wi = __shfl_sync(kFull, wv, i);
-                    uint64_t nmi[W];
+                    const int i1 = bal ? __ffs(bal) - 1 : -1;
+                    if (bal) bal &= bal - 1;
+                    const int j1 = i1 < 0 ? i0 : i1;
+                    const int w0 = __shfl_sync(kFull, wv, i0);
+                    const int w1 = __shfl_sync(kFull, wv, j1);
+                    uint64_t n0[W], n1[W];
 #pragma unroll
-                    for (int w = 0; w < W; ++w) nmi[w] = __shfl_sync(kFull, nm[w], i);
-                    double *srow = p.sigma + (size_t)wi * S;
+                    for (int w = 0; w < W; ++w) {
+                        n0[w] = __shfl_sync(kFull, nm[w], i0);
+                        n1[w] = __shfl_sync(kFull, nm[w], j1);
+                    }
+                    if (i1 < 0) {
+#pragma unroll
+                        for (int w = 0; w < W; ++w) n1[w] = 0ull;
+                    }
+                    double *r0 = p.sigma + (size_t)w0 * S;
+                    double *r1 = p.sigma + (size_t)w1 * S;
 #pragma unroll
                     for (int ii = 0; ii < PL; ++ii) {
                         const int s = lane + 32 * ii;
-                        if (mask_bit<W>(nmi, s)) atomicAdd(&srow[s], sig[ii]);
+                        if (mask_bit<W>(n0, s)) atomicAdd(&r0[s], sig[ii]);
+                        if (mask_bit<W>(n1, s)) atomicAdd(&r1[s], sig[ii]);
                     }
                 }
             }

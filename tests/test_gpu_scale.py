@@ -1,0 +1,118 @@
+"""Parity at full size, in the launch configuration bench.py times (tiles of
+128 sources, 128-arc chunks, hub-distance tile order).
+
+R-MAT scale 20 (the exact batch): RV lists of all 64 queries bit-exact;
+dist and sigma of sampled union sources bit-exact and their dependencies on
+every query within 1e-9; full BC(r) for the queries the oracle can finish.
+R-MAT scale 22 with 30 % reciprocal arcs (the sampled batch): the draws of
+eps = 0.01, delta = 0.1, seed 7 bit-exact, and the dependencies of drawn
+sources within 1e-9.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+
+
+def close(a, b):
+    return abs(a - b) <= REL * max(1.0, abs(b))
+
+
+@pytest.fixture(scope="module")
+def bcd():
+    import paper_1708_08739_gb300 as m
+    m.lib()
+    return m
+
+
+@pytest.fixture(scope="module")
+def rmat20(bcd):
+    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
+    qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=2, chunk_arcs=128)
+    return g, O.Graph.from_csr(g), dg, qs
+
+
+def test_rmat20_rv_lists(bcd, rmat20):
+    g, og, dg, qs = rmat20
+    seen = {}
+    for r in qs:
+        if r in seen:
+            continue
+        got = bcd.bc_rv_compute(dg, r)
+        seen[r] = got
+        assert np.array_equal(got, O.rv(og, r)), r
+
+
+def test_rmat20_sampled_sources(bcd, rmat20):
+    g, og, dg, qs = rmat20
+    top = qs[32]
+    union = O.rv(og, top)
+    rng = np.random.default_rng(5)
+    srcs = np.sort(rng.choice(union, size=12, replace=False)).astype(np.int32)
+    qv = np.array(list(dict.fromkeys(qs)), dtype=np.int32)[:64]
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, qv)
+    odep, ofl, _ = O.dependencies(og, srcs, qv, 0)
+    for i, s in enumerate(srcs.tolist()):
+        st = O.source_state(og, s)
+        assert np.array_equal(dist[i], st["dist"]), s
+        if not st["flags"]:
+            assert np.array_equal(sig[i], st["sigma"]), s
+        for j in range(qv.shape[0]):
+            if qv[j] != s:
+                assert close(dep[i, j], odep[i, j]), (s, int(qv[j]), dep[i, j], odep[i, j])
+
+
+def test_rmat20_small_queries_full(bcd, rmat20):
+    g, og, dg, qs = rmat20
+    small = []
+    for r in dict.fromkeys(qs):
+        k = bcd.bc_rv_compute(dg, r).shape[0]
+        if 0 < k <= 200:
+            small.append(r)
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in small])
+    for r, o in zip(small, out):
+        want, k, _ = O.bc_exact(og, r, 0)
+        assert o["rv_size"] == k and close(o["bc"], want), (r, o["bc"], want)
+
+
+@pytest.fixture(scope="module")
+def rmat22(bcd):
+    g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=2, chunk_arcs=128)
+    return g, O.Graph.from_csr(g), dg
+
+
+def test_rmat22_sampled_draws_and_dependencies(bcd, rmat22):
+    g, og, dg = rmat22
+    T = O.samples_for(0.01, 0.1)
+    assert T == 14979
+    qs = [int(x) for x in gg.random_vertices(g.n, 64, 105)]
+    checked = 0
+    for r in qs:
+        if g.out_degree()[r] == 0:
+            continue
+        draws, k = bcd.bc_draw_samples(dg, r, T, 7)
+        rvl = O.rv(og, r)
+        assert k == rvl.shape[0]
+        if k == 0:
+            continue
+        want = np.array([rvl[O.sample_index(7, t, k)] for t in range(T)], dtype=np.int32)
+        assert np.array_equal(draws, want), r
+        if checked == 0 and k > 1000:
+            srcs = np.array(sorted(set(want[:8].tolist())), dtype=np.int32)
+            dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, [r], want_sigma=False)
+            odep, _, _ = O.dependencies(og, srcs, [r], 0)
+            for i in range(srcs.shape[0]):
+                st = O.source_state(og, int(srcs[i]))
+                assert np.array_equal(dist[i], st["dist"])
+                assert close(dep[i, 0], odep[i, 0]), (int(srcs[i]), dep[i, 0], odep[i, 0])
+            checked += 1
+    assert checked == 1
