@@ -353,21 +353,23 @@ __device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const
     }
 }
 
-// Eq. 4 for the entries of level L (backward pass). The c rows of up to NB
-// tight heads are copied into the warp's shared-memory stage with 16-byte
-// cp.async transfers (one source pair per lane and mask word), then summed
-// in arc order.
+// Eq. 4 for the entries of level L (backward pass). For the tight heads of a
+// group of 32 arcs, only the 16-byte source pairs that hold a tight source
+// are copied (cp.async, L2) into the warp's shared-memory stage, packed head
+// after head, so that one round trip brings in a whole group; the sums then
+// run over the heads in arc order.
 template <int W>
 __device__ void backward_level(const TravParams &p, int L, long long cs, long long ccnt,
                                const uint64_t *s_active, const uint64_t *s_need, long long gwarp,
                                long long nwarps, double *stage, Stats &st) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
-    constexpr int NB = kStageBytes / (8 * S);
-    static_assert(NB >= 1 && NB <= 16, "stage holds 1..16 rows");
+    constexpr int KU = kStageBytes / 16;  // 16-byte units the stage holds
+    constexpr unsigned long long kEven = 0x5555555555555555ull;
     const int lane = threadIdx.x & 31;
     const int nx = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
+    const unsigned long long below = (lane == 0) ? 0ull : (~0ull >> (64 - 2 * lane));  // bits of pairs < lane
     ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + L], ccnt, nwarps);
     long long c;
     while (grab.next(c, lane)) {
@@ -407,40 +409,60 @@ __device__ void backward_level(const TravParams &p, int L, long long cs, long lo
             }
             unsigned bal = __ballot_sync(kFull, any);
             while (bal) {
-                unsigned bits[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) bits[w] = 0u;
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    int i = -1;
-                    if (bal) {
-                        i = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                    }
-                    const int sl = i < 0 ? 0 : i;
-                    const int wi = __shfl_sync(kFull, wv, sl);
-                    const double *crow = p.sigma + (size_t)wi * S;
+                // issue: tight heads in arc order until the stage is full
+                unsigned done = 0u;
+                int units = 0;
+                unsigned scan = bal;
+                while (scan) {
+                    const int i = __ffs(scan) - 1;
+                    int need = 0;
+                    uint64_t tmi[W];
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        const uint64_t tmi = __shfl_sync(kFull, tm[w], sl);
-                        const unsigned two = i < 0 ? 0u : (unsigned)((tmi >> (2 * lane)) & 3ull);
-                        bits[w] |= two << (2 * b);
-                        cp_async16(stage + b * S + 64 * w + 2 * lane, crow + 64 * w + 2 * lane, two ? 16 : 0);
+                        tmi[w] = __shfl_sync(kFull, tm[w], i);
+                        need += __popcll((tmi[w] | (tmi[w] >> 1)) & kEven);
                     }
+                    if (units + need > KU && units > 0) break;
+                    const int wi = __shfl_sync(kFull, wv, i);
+                    const double *crow = p.sigma + (size_t)wi * S;
+                    int off = units;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const uint64_t pm = (tmi[w] | (tmi[w] >> 1)) & kEven;
+                        if ((pm >> (2 * lane)) & 1ull) {
+                            const int slot = off + __popcll(pm & below);
+                            cp_async16(stage + 2 * slot, crow + 64 * w + 2 * lane, 16);
+                        }
+                        off += __popcll(pm);
+                    }
+                    units = off;
+                    done |= 1u << i;
+                    scan &= scan - 1;
                 }
                 cp_async_wait_all();
                 __syncwarp();
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
+                // consume the same heads in the same order
+                int offc = 0;
+                unsigned cons = done;
+                while (cons) {
+                    const int i = __ffs(cons) - 1;
+                    cons &= cons - 1;
 #pragma unroll
                     for (int w = 0; w < W; ++w) {
-                        const unsigned two = (bits[w] >> (2 * b)) & 3u;
-                        const double2 val = *reinterpret_cast<const double2 *>(stage + b * S + 64 * w + 2 * lane);
-                        if (two & 1u) acc[2 * w] += val.x;
-                        if (two & 2u) acc[2 * w + 1] += val.y;
+                        const uint64_t tmi = __shfl_sync(kFull, tm[w], i);
+                        const uint64_t pm = (tmi | (tmi >> 1)) & kEven;
+                        const unsigned two = (unsigned)((tmi >> (2 * lane)) & 3ull);
+                        if (two) {
+                            const int slot = offc + __popcll(pm & below);
+                            const double2 val = *reinterpret_cast<const double2 *>(stage + 2 * slot);
+                            if (two & 1u) acc[2 * w] += val.x;
+                            if (two & 2u) acc[2 * w + 1] += val.y;
+                        }
+                        offc += __popcll(pm);
                     }
                 }
                 __syncwarp();
+                bal &= ~done;
             }
         }
         if (nch == 1) {
