@@ -35,10 +35,12 @@ import graphgen as gg  # noqa: E402
 
 METRIC = "GTEPS and BC(r) queries/s (exact and sampled) vs HBM roofline; p50/p99 query latency"
 WORKLOAD = "rmat20_ef16_exact64"
-# dram bytes per (source x reached arc) of the traversal kernel, from the ncu
-# capture summarised in profiles/trav_kernel_rmat20.md; None when the kernel
-# has changed since that capture
-TRAFFIC_BYTES_PER_EDGE = None
+# dram bytes per (source x reached arc) of the traversal kernel, per workload
+# graph, from the ncu capture summarised in
+# profiles/trav_kernel_rmat20_sampled512_w2.md (R-MAT scale 20, 128-source
+# tiles); a workload without an entry, or a kernel changed since the capture,
+# reports traffic null
+TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 10.51}
 
 
 def log(*a):
@@ -276,7 +278,8 @@ def run_gpu(args):
     algo_bytes = 2.0 * (8.0 * vb + 4.0 * eb) + 40.0 * reached + 24.0 * tight
     peak, peak_kind = peaks()
     achieved = algo_bytes / (trav_ms / 1000.0) / 1e9
-    traffic = None if TRAFFIC_BYTES_PER_EDGE is None else TRAFFIC_BYTES_PER_EDGE * edges
+    tb = TRAFFIC_BYTES_PER_EDGE.get(args.workload) if args.tile_words == 2 else None
+    traffic = None if tb is None else tb * edges
 
     # end to end through the C ABI: pinned host CSR in, results out
     off_h = torch.from_numpy(g.offsets).pin_memory()
