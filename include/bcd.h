@@ -194,7 +194,7 @@ typedef struct {
     double ms_rv, ms_sample, ms_spd, ms_total;
     double ms_forward;        /* wall time of the traversal kernel's forward */
     double ms_backward;       /* ... and backward passes (one block's view) */
-    int64_t tiles;            /* tiles of 64*tile_words sources run */
+    int64_t tiles;            /* tiles run (64*tile_words sources each; 64*weighted_words on weighted graphs) */
     int32_t max_level;        /* deepest SPD level met */
     int32_t grid_blocks;      /* blocks of the persistent traversal launch */
     double ms_traversal;      /* CUDA-event time of the batched traversal launches */
@@ -295,7 +295,12 @@ void bc_server_destroy(bc_server *srv);
  *                  largest in-degree x out-degree, so that a tile's BFS
  *                  levels line up; 2 keeps ascending vertex ids;
  *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2
- *                  trades register spills for occupancy).
+ *                  trades register spills for occupancy);
+ *   weighted_words sources per tile of the weighted kernel, in words of 64
+ *                  (1, 2, 4, 8 or 16, with n * 64 * weighted_words <= 2^32).
+ *                  bc_graph_create picks the widest that fits in half of
+ *                  the free device memory at about 32 bytes per (vertex,
+ *                  source) pair. tile_words applies to unweighted graphs only.
  * Zero fields keep their current value.
  */
 typedef struct {
@@ -304,7 +309,8 @@ typedef struct {
     int32_t block_threads;
     int32_t source_order;
     int32_t blocks_per_sm;
-    int32_t reserved[3];
+    int32_t weighted_words;
+    int32_t reserved[2];
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);

@@ -75,7 +75,8 @@ class bc_batch_info(C.Structure):
 
 class bc_config(C.Structure):
     _fields_ = [("tile_words", C.c_int32), ("chunk_arcs", C.c_int32), ("block_threads", C.c_int32),
-                ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("weighted_words", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class bc_server_config(C.Structure):
@@ -221,8 +222,10 @@ def bc_set_stream(g: Graph, stream):
     _check(lib().bc_set_stream(g.handle, C.c_void_p(stream or 0)))
 
 
-def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0):
-    c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm))
+def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0,
+                  weighted_words=0):
+    c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm),
+                  int(weighted_words))
     _check(lib().bc_set_config(g.handle, C.byref(c)))
 
 
@@ -230,7 +233,7 @@ def bc_get_config(g: Graph) -> dict:
     c = bc_config()
     _check(lib().bc_get_config(g.handle, C.byref(c)))
     return {"tile_words": c.tile_words, "chunk_arcs": c.chunk_arcs, "block_threads": c.block_threads,
-            "source_order": c.source_order, "blocks_per_sm": c.blocks_per_sm}
+            "source_order": c.source_order, "blocks_per_sm": c.blocks_per_sm, "weighted_words": c.weighted_words}
 
 
 def bc_graph_info(g: Graph):

@@ -22,6 +22,7 @@ enum DevErr : int32_t {
     kDevSlotOverflow = 3,
     kDevTimeout = 4,
     kDevLevelOverflow = 5,
+    kDevBucketOverflow = 6,
 };
 
 // Per-launch control block of the persistent traversal kernel.
@@ -83,7 +84,8 @@ struct TravParams {
     double *sigma;      // [n * S] sigma, then c = (1 + delta) / sigma in place
     // level history
     int32_t *hv;        // [hcap]
-    uint64_t *hm;       // [hcap * W]
+    uint64_t *hm;       // [hcap * W] (unweighted)
+    uint16_t *hs;       // [hcap] source slot of an entry (weighted)
     int64_t *hslot;     // [hcap]
     int64_t hcap;
     Chunk *chunks;      // [ccap]
@@ -117,12 +119,11 @@ struct TravParams {
     const int32_t *rcol;     // [m]
     const uint32_t *rwt;     // [m] weights of R(G)'s arcs
     uint64_t *dist;          // [n * S] tentative, then final distances (UINT64_MAX unreached)
-    uint32_t *qbits;         // [n * ring / 32] bucket slots a vertex is queued in
-    int32_t *buckets;        // [ring * bcap]
-    unsigned long long *bcount;  // [ring]
-    int64_t bcap;
+    uint32_t *buckets;       // [ring * bcap] queued pairs (vertex << log2 S | source slot), circular per slot
+    unsigned long long *bcount;  // [2 * ring] entries ever queued per slot, then entries consumed per slot
+    int64_t bcap;            // entries per slot (a power of two)
     int32_t ring;            // power of two above the largest weight
-    int32_t pad2;
+    int32_t nw;              // 64-source words of a weighted tile (1, 2, 4, 8 or 16)
     int64_t *lev_dist;       // [maxlev + 2] distance of each non-empty level
     // reach mode output
     uint64_t *rvmask;        // [n]
@@ -149,6 +150,8 @@ struct bcd_workspace {
     // history
     int32_t *hv = nullptr;
     uint64_t *hm = nullptr;
+    int64_t hmcap = 0;            // entries hm holds (hcap but on weighted graphs)
+    uint16_t *hs = nullptr;
     int64_t *hslot = nullptr;
     int64_t hcap = 0;
     bcd::Chunk *chunks = nullptr;
@@ -169,18 +172,18 @@ struct bcd_workspace {
     int32_t *posd = nullptr;      // [n] position of a vertex in the source union
     int32_t *hublev = nullptr;    // [n] hop distance to the hub (tile ordering key), -1 unreached
     // weighted graphs
-    uint64_t *dist = nullptr;     // [n * 64]
-    uint32_t *qbits = nullptr;    // [n * ring / 32]
-    int32_t *buckets = nullptr;   // [ring * n]
-    unsigned long long *bcount = nullptr;  // [ring]
+    uint64_t *dist = nullptr;     // [n * 64 * W]
+    uint32_t *buckets = nullptr;  // [ring * bcap]
+    unsigned long long *bcount = nullptr;  // [2 * ring]
+    int64_t bcap = 0;
     int64_t *lev_dist = nullptr;  // [maxlev + 2]
     int32_t ring = 0;
     int32_t hub = -1;             // vertex the ordering key is measured to
-    int32_t *dlist = nullptr;     // [n + 64*4] source union, padded to whole tiles
-    int32_t *qlevel = nullptr;    // [256 * 64]
-    double *dep = nullptr;        // [256 * 64]
+    int32_t *dlist = nullptr;     // [n + 64 * W + 256] source union, padded to whole tiles
+    int32_t *qlevel = nullptr;    // [64 * W * 64]
+    double *dep = nullptr;        // [64 * W * 64]
     uint32_t *qflags = nullptr;   // [64]
-    uint64_t *srcflag = nullptr;  // [4]
+    uint64_t *srcflag = nullptr;  // [W]
     bcd::Counters *ctr = nullptr;
     int64_t *scratch64 = nullptr; // [scratch_len + 256] scan/compaction scratch, counts past scratch_len
     int64_t scratch_len = 0;
@@ -226,7 +229,8 @@ struct bc_graph {
     std::vector<int64_t> h_off;   // forward offsets (degree checks)
     std::vector<int64_t> h_roff;  // reverse offsets
     std::vector<int32_t> h_hublev; // host copy of the tile ordering key
-    int tile_words = 1;           // W of the SPD kernel
+    int tile_words = 1;           // W of the SPD kernel (unweighted graphs)
+    int weighted_words = 1;       // 64-source words of a weighted tile
     int chunk_arcs = 128;
     int source_order = 1;         // 1: tiles ordered by distance to the hub, 0: by vertex id
     int blocks_per_sm = 1;        // resident blocks per SM of the 256-source kernel (1 or 2)
@@ -264,6 +268,8 @@ bc_status ensure_workspace(bc_graph *g, int W);
 bc_status grow_history(bc_graph *g);
 bc_status alloc_levels(bc_graph *g, int64_t maxlev);
 bc_status grow_levels(bc_graph *g);
+bc_status grow_buckets(bc_graph *g);
+int tile_words_of(const bc_graph *g);  // mask words of the tiles the graph's kernel runs
 void free_workspace(bc_graph *g);
 
 // traversal launcher (bcd_traverse.cu)

@@ -137,6 +137,12 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->blocks_per_sm && c->blocks_per_sm != 1 && c->blocks_per_sm != 2)
         return set_error(BC_E_INVALID_ARG, "bc_set_config: blocks_per_sm must be 1 or 2");
     if (c->blocks_per_sm) g->blocks_per_sm = c->blocks_per_sm;
+    if (c->weighted_words) {
+        const int w = c->weighted_words;
+        if (w < 1 || w > 16 || (w & (w - 1)) || (((uint64_t)g->n) << 6) * (uint64_t)w > (1ull << 32))
+            return set_error(BC_E_INVALID_ARG, "bc_set_config: weighted_words must be 1, 2, 4, 8 or 16 with n * 64 * weighted_words <= 2^32");
+        g->weighted_words = w;
+    }
     if (c->tile_words) g->tile_words = c->tile_words;
     if (c->chunk_arcs) g->chunk_arcs = c->chunk_arcs;
     if (c->block_threads) g->block_threads = c->block_threads;
@@ -150,7 +156,8 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->block_threads = g->block_threads;
     c->source_order = g->source_order == 1 ? 1 : 2;
     c->blocks_per_sm = g->blocks_per_sm;
-    c->reserved[0] = c->reserved[1] = c->reserved[2] = 0;
+    c->weighted_words = g->weighted_words;
+    c->reserved[0] = c->reserved[1] = 0;
     return BC_OK;
 }
 
@@ -266,6 +273,21 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
     if (ce != cudaSuccess) return fail(cuda_error(ce, "build reverse graph"));
     if ((ce = cudaGetLastError()) != cudaSuccess) return fail(cuda_error(ce, "graph kernels"));
     g->launches += 5;
+    if (g->weighted) {
+        // widest weighted tile (up to 1024 sources) whose per-pair state
+        // (dist, sigma, history, bucket share: about 32 bytes) fits in half of
+        // the free device memory, with vertex << log2(S) in 32 bits
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        int nw = 16;
+        while (nw > 1 && ((((uint64_t)d->n) << 6) * (uint64_t)nw > (1ull << 32) ||
+                          (double)d->n * 64.0 * nw * 32.0 > 0.5 * (double)fr))
+            nw >>= 1;
+        g->weighted_words = nw;
+    }
     *out = g;
     return BC_OK;
 }

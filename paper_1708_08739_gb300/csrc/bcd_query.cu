@@ -164,23 +164,34 @@ __global__ void reduce_tiles(const double *tile_partial, int64_t ntiles, const d
 // workspace
 // ---------------------------------------------------------------------------
 
-static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t pcap) {
+// Level history and chunk lists. Unweighted entries carry a W-word source
+// mask and chunked rows a partial-row slot; weighted entries carry one source
+// slot, and the partial sums of their long rows are indexed by chunk. On a
+// weighted graph the masks serve only the one-word reach traversals (RV and
+// the tile order), which get their own, smaller capacity hmcap.
+static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t pcap, int64_t hmcap) {
     bcd_workspace &ws = g->ws;
     dev_free(ws.hv);
     dev_free(ws.hm);
+    dev_free(ws.hs);
     dev_free(ws.hslot);
     dev_free(ws.chunks);
     dev_free(ws.partial);
     dev_free(ws.pdone);
     if (hcap >= (int64_t)INT32_MAX) hcap = (int64_t)INT32_MAX - 1;
+    const bool wg = g->weighted;
+    if (wg) pcap = ccap;
+    hmcap = wg ? std::min(hmcap, hcap) : hcap;
+    ws.hmcap = hmcap;
     ws.hcap = hcap;
     ws.ccap = ccap;
     ws.pcap = pcap;
     BCD_TRY(dev_alloc(&ws.hv, (size_t)hcap));
-    BCD_TRY(dev_alloc(&ws.hm, (size_t)hcap * ws.W));
-    BCD_TRY(dev_alloc(&ws.hslot, (size_t)hcap));
+    BCD_TRY(dev_alloc(&ws.hm, wg ? (size_t)hmcap : (size_t)hcap * ws.W));
+    BCD_TRY(dev_alloc(&ws.hs, wg ? (size_t)hcap : (size_t)1));
+    BCD_TRY(dev_alloc(&ws.hslot, wg ? (size_t)1 : (size_t)hcap));
     BCD_TRY(dev_alloc(&ws.chunks, (size_t)ccap));
-    BCD_TRY(dev_alloc(&ws.partial, (size_t)pcap * 64 * ws.W));
+    BCD_TRY(dev_alloc(&ws.partial, wg ? (size_t)pcap : (size_t)pcap * 64 * ws.W));
     BCD_TRY(dev_alloc(&ws.pdone, (size_t)pcap));
     BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)pcap, g->stream));
     return BC_OK;
@@ -200,13 +211,13 @@ bc_status alloc_levels(bc_graph *g, int64_t maxlev) {
     const size_t L = (size_t)maxlev + 2;
     BCD_TRY(dev_alloc(&ws.lev_cnt, L));
     BCD_TRY(dev_alloc(&ws.lev_ccnt, L));
-    BCD_TRY(dev_alloc(&ws.lev_grab, 2 * L));
+    BCD_TRY(dev_alloc(&ws.lev_grab, 6 * L));
     BCD_TRY(dev_alloc(&ws.lev_start, L));
     BCD_TRY(dev_alloc(&ws.lev_cstart, L));
     if (g->weighted) BCD_TRY(dev_alloc(&ws.lev_dist, L));
     BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * L, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * L, g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 2 * L, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 6 * L, g->stream));
     return BC_OK;
 }
 
@@ -216,6 +227,8 @@ bc_status grow_levels(bc_graph *g) {
     return alloc_levels(g, std::min<int64_t>(cur * 4, (int64_t)INT32_MAX / 4));
 }
 
+// Distance slab and bucket ring of the weighted kernel. A tile settles each
+// (vertex, source) pair once, so the history holds up to n * S entries.
 bc_status ensure_weighted_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (ws.dist) return BC_OK;
@@ -224,23 +237,41 @@ bc_status ensure_weighted_state(bc_graph *g) {
     if (R > 4096) return set_error(BC_E_INVALID_ARG, "weighted graphs need arc weights of at most 4095");
     ws.ring = R;
     const size_t n = (size_t)g->n;
-    BCD_TRY(dev_alloc(&ws.dist, n * 64));
-    BCD_TRY(dev_alloc(&ws.qbits, n * (size_t)(R / 32)));
-    BCD_TRY(dev_alloc(&ws.buckets, n * (size_t)R));
-    BCD_TRY(dev_alloc(&ws.bcount, (size_t)R));
-    BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * n * 64, g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.qbits, 0, sizeof(uint32_t) * n * (size_t)(R / 32), g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * (size_t)R, g->stream));
-    // a weighted tile usually settles a vertex once per source
-    if (ws.hcap < 32 * (int64_t)n + 4096) BCD_TRY(alloc_history(g, 32 * (int64_t)n + 4096, ws.ccap, ws.pcap));
+    const size_t S = 64 * (size_t)ws.W;
+    int64_t bcap = 1 << 14;
+    while ((size_t)bcap * 256 < n * S) bcap *= 2;
+    ws.bcap = bcap;
+    BCD_TRY(dev_alloc(&ws.dist, n * S));
+    BCD_TRY(dev_alloc(&ws.buckets, (size_t)R * (size_t)bcap));
+    BCD_TRY(dev_alloc(&ws.bcount, 2 * (size_t)R));
+    BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * n * S, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * 2 * (size_t)R, g->stream));
+    const int64_t hneed = std::min<int64_t>((int64_t)(n * S) + 4096, (int64_t)INT32_MAX - 1);
+    if (ws.hcap < hneed) BCD_TRY(alloc_history(g, hneed, ws.ccap, ws.pcap, ws.hmcap));
+    return BC_OK;
+}
+
+// Doubles the entries per slot of the bucket ring (pending pairs of one
+// distance outgrew it).
+bc_status grow_buckets(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    if (ws.bcap >= ((int64_t)1 << 34)) return set_error(BC_E_OOM, "bucket ring: too many pending pairs at one distance");
+    dev_free(ws.buckets);
+    ws.bcap *= 2;
+    BCD_TRY(dev_alloc(&ws.buckets, (size_t)ws.ring * (size_t)ws.bcap));
+    BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * 2 * (size_t)ws.ring, g->stream));
     return BC_OK;
 }
 
 bc_status grow_history(bc_graph *g) {
     bcd_workspace &ws = g->ws;
-    if (ws.hcap >= (int64_t)INT32_MAX - 1) return set_error(BC_E_OOM, "level history exceeds 2^31 entries");
-    return alloc_history(g, ws.hcap * 2, ws.ccap * 2, ws.pcap * 2);
+    if (ws.hcap >= (int64_t)INT32_MAX - 1 && ws.hmcap >= ws.hcap && ws.ccap >= ((int64_t)1 << 34))
+        return set_error(BC_E_OOM, "level history exceeds 2^31 entries");
+    return alloc_history(g, std::min<int64_t>(ws.hcap * 2, (int64_t)INT32_MAX - 1), ws.ccap * 2, ws.pcap * 2,
+                         ws.hmcap * 2);
 }
+
+int tile_words_of(const bc_graph *g) { return g->weighted ? g->weighted_words : g->tile_words; }
 
 void free_workspace(bc_graph *g) {
     bcd_workspace &ws = g->ws;
@@ -249,6 +280,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.sigma);
     dev_free(ws.hv);
     dev_free(ws.hm);
+    dev_free(ws.hs);
     dev_free(ws.hslot);
     dev_free(ws.chunks);
     dev_free(ws.partial);
@@ -264,7 +296,6 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.posd);
     dev_free(ws.hublev);
     dev_free(ws.dist);
-    dev_free(ws.qbits);
     dev_free(ws.buckets);
     dev_free(ws.bcount);
     dev_free(ws.lev_dist);
@@ -293,12 +324,13 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     ws.W = W;
     ws.n = n;
     ws.m = m;
-    ws.vs_stride = ((3 * W + 3) / 4) * 4;
+    // the weighted kernel keeps no masks; the one-word reach traversals do
+    ws.vs_stride = g->weighted ? 4 : ((3 * W + 3) / 4) * 4;
     BCD_TRY(dev_alloc(&ws.vs, (size_t)n * ws.vs_stride));
     BCD_TRY(dev_alloc(&ws.tag, (size_t)n));
     BCD_TRY(dev_alloc(&ws.sigma, (size_t)n * 64 * W));
     const int64_t ch = g->chunk_arcs;
-    BCD_TRY(alloc_history(g, 8 * n + 4096, 8 * n + 8 * (m / ch) + 4096, 8 * (m / ch) + 4096));
+    BCD_TRY(alloc_history(g, 8 * n + 4096, 8 * n + 8 * (m / ch) + 4096, 8 * (m / ch) + 4096, 16 * n + 4096));
     BCD_TRY(alloc_levels(g, std::min<int64_t>(g->weighted ? std::max<int64_t>(n + 1, 65536) : n + 1,
                                               (int64_t)INT32_MAX / 4)));
     BCD_TRY(dev_alloc(&ws.rvmask, (size_t)n));
@@ -307,11 +339,11 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.posd, (size_t)n));
     BCD_TRY(dev_alloc(&ws.hublev, (size_t)n));
     ws.hub = -1;
-    BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 256));
-    BCD_TRY(dev_alloc(&ws.qlevel, 256 * 64));
-    BCD_TRY(dev_alloc(&ws.dep, 256 * 64));
+    BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 64 * (size_t)W + 256));  // union padded to whole tiles
+    BCD_TRY(dev_alloc(&ws.qlevel, (size_t)64 * W * 64));
+    BCD_TRY(dev_alloc(&ws.dep, (size_t)64 * W * 64));
     BCD_TRY(dev_alloc(&ws.qflags, 64));
-    BCD_TRY(dev_alloc(&ws.srcflag, 4));
+    BCD_TRY(dev_alloc(&ws.srcflag, (size_t)std::max(W, 4)));
     BCD_TRY(dev_alloc(&ws.ctr, 1));
     ws.scratch_len = scan_scratch_len(n) + 64;
     BCD_TRY(dev_alloc(&ws.scratch64, (size_t)ws.scratch_len + 256));
@@ -320,7 +352,7 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_CUDA(cudaMemsetAsync(ws.rvmask, 0, sizeof(uint64_t) * (size_t)n, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.need, 0, sizeof(uint64_t) * (size_t)n, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.qmask, 0, sizeof(uint64_t) * (size_t)n, g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 64 * W * 64, g->stream));
     BCD_CUDA(cudaMallocHost(&ws.pinned, 1 << 20));
     ws.pinned_cap = 1 << 20;
     return BC_OK;
@@ -522,7 +554,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
     const int nq = (int)qs.size();
-    const int W = g->weighted ? 1 : g->tile_words;
+    const int W = tile_words_of(g);
     const int S = 64 * W;
     // the ordering key's reach traversal uses the union buffer: run it first
     if (g->source_order == 1) BCD_TRY(ensure_hub_levels(g));
@@ -801,7 +833,7 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
                     uint32_t *qflags, unsigned long long *edges) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
-    const int S = 64 * (g->weighted ? 1 : g->tile_words);
+    const int S = 64 * tile_words_of(g);
     const int64_t ntiles = (int64_t)srcs.size() / S;
     if (ntiles * S != (int64_t)srcs.size() || ntiles == 0) return set_error(BC_E_INTERNAL, "run_slice: ragged slice");
     std::vector<int32_t> vs;
@@ -842,7 +874,7 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
     p.qflags = ws.qflags;
     p.srcflag = ws.srcflag;
     g->launches += 1;
-    BCD_TRY(run_traversal(g, g->weighted ? 1 : g->tile_words, p, nullptr, edges));
+    BCD_TRY(run_traversal(g, tile_words_of(g), p, nullptr, edges));
     partials.resize((size_t)ntiles * 64);
     BCD_CUDA(cudaMemcpyAsync(partials.data(), ws.tile_partial, sizeof(double) * partials.size(), cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaMemcpyAsync(qflags, ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -860,7 +892,7 @@ bc_status prepare_ordering(bc_graph *g) { return g->source_order == 1 ? ensure_h
 
 bc_status check_graph(bc_graph *g, const char *fn) {
     if (!g) return set_error(BC_E_INVALID_ARG, std::string(fn) + ": NULL graph");
-    BCD_TRY(ensure_workspace(g, g->tile_words));
+    BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     if (g->weighted) BCD_TRY(ensure_weighted_state(g));
     return BC_OK;
 }
@@ -1040,7 +1072,7 @@ bc_status bc_rv_compute(bc_graph *g, int32_t r, int32_t *out, int64_t cap, int64
     if (!g || !count) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: NULL argument");
     if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: vertex out of range");
     if (cap < 0 || (cap > 0 && !out)) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: bad output buffer");
-    BCD_TRY(ensure_workspace(g, g->tile_words));
+    BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     std::vector<int64_t> sizes;
     BCD_TRY(reach_roots(g, std::vector<int32_t>{r}, sizes));
     *count = sizes[0];
@@ -1058,7 +1090,7 @@ bc_status bc_draw_samples(bc_graph *g, int32_t r, int64_t T, uint64_t seed, int3
     if (!g || !rv_size) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: NULL argument");
     if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: vertex out of range");
     if (T < 1 || T > 4000000000ll || !out) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: bad T or output");
-    BCD_TRY(ensure_workspace(g, g->tile_words));
+    BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     *rv_size = 0;
     if (g->h_off[r + 1] == g->h_off[r]) return BC_OK;
     std::vector<int64_t> sizes;
@@ -1094,7 +1126,7 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
     BCD_TRY(check_graph(g, "bc_spd_probe"));
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
-    const int W = g->weighted ? 1 : ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
+    const int W = ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
     const int S = 64 * W;
     for (int i = 0; i < nsrc; ++i) {
         if (sources[i] < 0 || sources[i] >= g->n) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: source out of range");
@@ -1123,7 +1155,7 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
     if (!nb.empty()) set_bits<<<(unsigned)((nb.size() + 255) / 256), 256, 0, s>>>(ws.need, d_nb, (int)nb.size(), 0);
     if (!qb.empty()) set_bits<<<1, 64, 0, s>>>(ws.qmask, d_nb + nb.size(), (int)qb.size(), 0);
     BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, 64));
-    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, s));
+    BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * S * 64, s));
     BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
     TravParams p;
     memset(&p, 0, sizeof(p));
@@ -1144,7 +1176,31 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
     if (dist || sigma || flags) {
         p.flags = kFlagNoBackward | kFlagNoReset;
         st = run_traversal(g, W, p, nullptr, nullptr);
-        if (st == BC_OK) {
+        if (st == BC_OK && g->weighted) {
+            // export the first nsrc columns of the dist and sigma slabs [v][S]
+            const size_t n = (size_t)g->n;
+            std::vector<uint64_t> wd(dist ? n * nsrc : 0);
+            std::vector<double> sg(sigma ? n * nsrc : 0);
+            std::vector<uint64_t> sf(W);
+            if (dist)
+                BCD_CUDA(cudaMemcpy2DAsync(wd.data(), sizeof(uint64_t) * nsrc, ws.dist, sizeof(uint64_t) * S,
+                                           sizeof(uint64_t) * nsrc, n, cudaMemcpyDeviceToHost, s));
+            if (sigma)
+                BCD_CUDA(cudaMemcpy2DAsync(sg.data(), sizeof(double) * nsrc, ws.sigma, sizeof(double) * S,
+                                           sizeof(double) * nsrc, n, cudaMemcpyDeviceToHost, s));
+            BCD_CUDA(cudaMemcpyAsync(sf.data(), ws.srcflag, sizeof(uint64_t) * W, cudaMemcpyDeviceToHost, s));
+            cudaError_t ce = cudaStreamSynchronize(s);
+            if (ce != cudaSuccess) st = cuda_error(ce, "probe export");
+            if (st == BC_OK) {
+                for (int i = 0; i < nsrc; ++i)
+                    for (size_t v = 0; v < n; ++v) {
+                        if (dist) dist[(size_t)i * n + v] = wd[v * nsrc + i];
+                        if (sigma) sigma[(size_t)i * n + v] = sg[v * nsrc + i];
+                    }
+                if (flags)
+                    for (int i = 0; i < nsrc; ++i) flags[i] = ((sf[i >> 6] >> (i & 63)) & 1ull) ? BC_FLAG_SIGMA_2_53 : 0u;
+            }
+        } else if (st == BC_OK) {
             // export sigma [v][S] and the level history
             const size_t n = (size_t)g->n;
             std::vector<double> sg;
@@ -1158,8 +1214,6 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
             cudaMemcpyAsync(sf.data(), ws.srcflag, sizeof(uint64_t) * W, cudaMemcpyDeviceToHost, s);
             cudaError_t ce = cudaStreamSynchronize(s);
             if (ce != cudaSuccess) st = cuda_error(ce, "probe export");
-            // every recorded level (a weighted level can be empty: all its queued
-            // vertices were superseded by shorter distances)
             int64_t total = 0;
             const int levels = (int)std::min<unsigned long long>(g->last.levels_max + 1, (unsigned long long)ws.maxlev + 1);
             for (int L = 0; L < levels; ++L) total += (int64_t)lc[L];
@@ -1174,19 +1228,13 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
             if (st == BC_OK) {
                 if (dist) std::fill(dist, dist + (size_t)nsrc * n, ~0ull);
                 if (sigma) std::fill(sigma, sigma + (size_t)nsrc * n, 0.0);
-                std::vector<uint64_t> wd;
-                if (g->weighted && dist) {
-                    wd.resize(n * 64);
-                    BCD_CUDA(cudaMemcpyAsync(wd.data(), ws.dist, sizeof(uint64_t) * n * 64, cudaMemcpyDeviceToHost, s));
-                    BCD_CUDA(cudaStreamSynchronize(s));
-                }
                 int64_t e = 0;
                 for (int L = 0; L < levels; ++L) {
                     for (unsigned long long k = 0; k < lc[L]; ++k, ++e) {
                         const int32_t v = hv[e];
                         for (int i = 0; i < nsrc; ++i) {
                             if ((hm[e * W + (i >> 6)] >> (i & 63)) & 1ull) {
-                                if (dist) dist[(size_t)i * n + v] = g->weighted ? wd[(size_t)v * 64 + i] : (uint64_t)L;
+                                if (dist) dist[(size_t)i * n + v] = (uint64_t)L;
                                 if (sigma) sigma[(size_t)i * n + v] = sg[(size_t)v * S + i];
                             }
                         }
@@ -1201,11 +1249,11 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
     }
     if (st == BC_OK && dep) {
         p.flags = 0;
-        BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * 256 * 64, s));
+        BCD_CUDA(cudaMemsetAsync(ws.dep, 0, sizeof(double) * S * 64, s));
         st = run_traversal(g, W, p, nullptr, nullptr);
         if (st == BC_OK) {
-            std::vector<double> hd(256 * 64);
-            BCD_CUDA(cudaMemcpyAsync(hd.data(), ws.dep, sizeof(double) * 256 * 64, cudaMemcpyDeviceToHost, s));
+            std::vector<double> hd((size_t)S * 64);
+            BCD_CUDA(cudaMemcpyAsync(hd.data(), ws.dep, sizeof(double) * S * 64, cudaMemcpyDeviceToHost, s));
             BCD_CUDA(cudaStreamSynchronize(s));
             for (int i = 0; i < nsrc; ++i)
                 for (int j = 0; j < nt; ++j) dep[(size_t)i * nt + j] = hd[i * 64 + j];

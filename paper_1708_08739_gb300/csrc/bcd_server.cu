@@ -170,7 +170,7 @@ bool bc_server::admit() {
 // Runs one slice of tiles from the pending pool. Returns false when idle.
 bool bc_server::run_slice_once() {
     if (nactive == 0) return false;
-    const int S = 64 * (g->weighted ? 1 : g->tile_words);
+    const int S = 64 * bcd::tile_words_of(g);
     const int64_t cap = (int64_t)cfg.tiles_per_slice * S;
     std::vector<int32_t> take;
     std::vector<uint64_t> need;

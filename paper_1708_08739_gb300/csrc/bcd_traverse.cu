@@ -735,12 +735,11 @@ bc_status reset_dense_state(bc_graph *g) {
     BCD_CUDA(cudaMemsetAsync(ws.sigma, 0, sizeof(double) * (size_t)ws.n * 64 * ws.W, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 2 * (size_t)(ws.maxlev + 2), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 6 * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)ws.pcap, g->stream));
     if (ws.dist) {
-        BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * (size_t)ws.n * 64, g->stream));
-        BCD_CUDA(cudaMemsetAsync(ws.qbits, 0, sizeof(uint32_t) * (size_t)ws.n * (ws.ring / 32), g->stream));
-        BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * (size_t)ws.ring, g->stream));
+        BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * (size_t)ws.n * 64 * ws.W, g->stream));
+        BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * 2 * (size_t)ws.ring, g->stream));
     }
     return BC_OK;
 }
@@ -755,7 +754,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.hv = ws.hv;
         p.hm = ws.hm;
         p.hslot = ws.hslot;
-        p.hcap = ws.hcap;
+        p.hcap = p.mode == kModeReach ? ws.hmcap : ws.hcap;
         p.chunks = ws.chunks;
         p.ccap = ws.ccap;
         p.partial = ws.partial;
@@ -784,12 +783,15 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             p.roff = g->d_roff;
             p.rcol = g->d_rcol;
             p.rwt = g->d_rw;
+            if (W < 1 || W > 16 || (W & (W - 1)) || W > ws.W || ((uint64_t)g->n << 6) * (uint64_t)W > (1ull << 32))
+                return set_error(BC_E_INVALID_ARG, "weighted tiles: 1, 2, 4, 8 or 16 words, n * 64 * words <= 2^32");
             p.dist = ws.dist;
-            p.qbits = ws.qbits;
+            p.hs = ws.hs;
             p.buckets = ws.buckets;
             p.bcount = ws.bcount;
-            p.bcap = g->n;
+            p.bcap = ws.bcap;
             p.ring = ws.ring;
+            p.nw = W;
             p.lev_dist = ws.lev_dist;
             st = launch_weighted(g, p);
         } else if (W == 1) {
@@ -830,6 +832,13 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         if (c.err == kDevTimeout) {
             reset_dense_state(g);
             return set_error(BC_E_TIMEOUT, "traversal: a grid barrier wait timed out");
+        }
+        if (c.err == kDevBucketOverflow) {
+            // more pending pairs at one distance than a ring slot holds: grow and rerun
+            BCD_TRY(grow_buckets(g));
+            BCD_TRY(reset_dense_state(g));
+            if (p.qflags) BCD_CUDA(cudaMemsetAsync(p.qflags, 0, sizeof(uint32_t) * 64, g->stream));
+            continue;
         }
         if (c.err == kDevLevelOverflow) {
             // more non-empty levels than the arrays hold (integer weights): grow and rerun

@@ -1,24 +1,34 @@
 // Weighted single-source work (Section 2 with positive integer weights, the
-// SPD of each source) for a tile of 64 sources: exact distances by Dial's
-// bucket order, sigma by a pull over tight in-arcs, and the dependencies of
-// Eq. 4 by a pull over tight out-arcs.
+// SPD of each source) for a tile of S = 64 * nw sources (nw = 1, 2, 4, 8 or
+// 16): exact distances in Dial's bucket order, sigma by a pull over tight
+// in-arcs, and the dependencies of Eq. 4 by a pull over tight out-arcs.
 //
-// Distances are integers, so processing distance values in increasing order
-// settles every (vertex, source) pair once: a relaxation lowers
-// dist[w][s] with atomicMin and queues w in the ring slot of its new
-// tentative distance (ring size a power of two above the largest weight, one
-// queued-bit per vertex and slot); when the slot's distance comes up, the
-// vertex is settled for exactly the sources whose distance equals it.
-// sigma_s(v) is pulled over in-arcs (u, v) with dist_s(u) + w(u, v) =
-// dist_s(v) (all such u are settled earlier), summed by warp trees and fp64
-// atomic adds of integers (exact below 2^53). The backward pass walks the
-// non-empty distance levels from the deepest, with arc (v, w) tight for s when
-// dist_s(v) + w(v, w) = dist_s(w), summing c_s(w) = (1 + delta_s(w)) /
-// sigma_s(w) in a fixed order per chunk and chunks in chunk order.
+// Distances are integers, so handling distance values in increasing order
+// settles every (vertex, source) pair once, at its final distance: a
+// relaxation that lowers dist_s(y) (atomicMin) queues the pair (y, s) in the
+// ring slot of the new distance. The ring has R slots, R a power of two above
+// the largest weight, so the distances in flight [d, d + R) never share a
+// slot. Each slot is a circular buffer: entries between its consumed base and
+// its count are pending. When slot d comes up, a pending pair whose distance
+// still equals d is settled; a pair lowered since it was queued is stale and
+// skipped. Every tight in-arc predecessor of a pair settled at d sits at a
+// distance below d, so sigma_s(v) is complete when it is pulled.
 //
-// Sources settle a vertex at many different distances, so a tile entry
-// usually carries one or two sources: lanes map to arcs, and the sources of
-// an entry are looped over.
+// The unit of work is one (vertex, source) pair. Lanes take pairs, so a warp
+// runs 32 independent chains of loads: a tile settles each vertex at as many
+// distances as it has sources, and sources rarely share a distance. A pair
+// whose vertex has more than 32 in- or out-arcs is cut into chunks of
+// chunk_arcs arcs that warps take after a grid barrier (lanes over arcs);
+// their sigma partial sums meet in fp64 atomic adds (integers: exact in any
+// order below 2^53, and the running sum shows when 2^53 is passed).
+//
+// The backward pass walks the distance levels from the deepest, down to the
+// shallowest level at which a query vertex sits for a source of the tile.
+// Arc (v, y) is tight for s when dist_s(v) + w(v, y) = dist_s(y);
+// c_s(y) = (1 + delta_s(y)) / sigma_s(y) replaces sigma in place. A short row
+// is summed by one lane in CSR order, a long row per lane in a fixed arc
+// order, then by a fixed butterfly per chunk, and the chunks are combined in
+// chunk order by the last one to finish, so delta is run-to-run reproducible.
 #include "bcd_common.cuh"
 #include "bcd_device.cuh"
 
@@ -28,7 +38,20 @@ namespace {
 
 using namespace dev;
 
-constexpr int WS = 64;  // sources per weighted tile
+constexpr int kMaxWords = 16;  // largest tile: 1024 sources
+constexpr int kShortRow = 32;  // rows of at most this many arcs are walked by one lane
+constexpr double kTwo53 = 9007199254740992.0;
+
+// Per-level counters of the weighted kernel: counter k of level l sits at
+// lev_grab[k * (maxlev + 2) + l].
+enum WLev : int {
+    kGrabPairs = 0,    // forward: hand-out of 32-pair groups of the level's slot
+    kChunksF = 1,      // forward: chunks of long rows emitted
+    kGrabChunksF = 2,  // forward: hand-out of those chunks
+    kGrabEntries = 3,  // backward: hand-out of 32-entry groups of the level
+    kChunksB = 4,      // backward: chunks of long rows emitted
+    kGrabChunksB = 5,  // backward: hand-out of those chunks
+};
 
 struct WStats {
     unsigned edges = 0, reached = 0, tight = 0, arcs = 0, vb = 0, eb = 0;
@@ -56,57 +79,183 @@ __device__ __forceinline__ double warp_sum(double x) {
     return x;
 }
 
-__device__ __forceinline__ void wqueue(const TravParams &p, int w, unsigned long long nd) {
+struct Tile {
+    int S;      // sources per tile
+    int shift;  // log2(S)
+};
+
+// Queues the pair (y, s) at tentative distance nd (slot positions wrap
+// around the slot's capacity; overflow is detected when the slot is read).
+__device__ __forceinline__ void wenqueue(const TravParams &p, const Tile &t, int y, int s, unsigned long long nd) {
     const int slot = (int)(nd & (unsigned long long)(p.ring - 1));
-    uint32_t *qb = p.qbits + (size_t)w * (p.ring >> 5) + (slot >> 5);
-    const uint32_t bit = 1u << (slot & 31);
-    if (!(atomicOr(qb, bit) & bit)) {
-        const unsigned long long pos = atomicAdd(&p.bcount[slot], 1ull);
-        if ((long long)pos < p.bcap)
-            p.buckets[(size_t)slot * p.bcap + pos] = w;
-        else
-            set_err(p.ctr, kDevHistOverflow);
+    const unsigned long long pos = atomicAdd(&p.bcount[slot], 1ull);
+    p.buckets[(size_t)slot * p.bcap + (size_t)(pos & (unsigned long long)(p.bcap - 1))] =
+        ((uint32_t)y << t.shift) | (uint32_t)s;
+}
+
+// The graph arrays do not change during a launch, so their loads take the
+// read-only path (cached in L1; a lane walking its own row reuses sectors).
+// The per-arc loops handle arcs in groups of four whose loads are issued
+// together; sums still run in arc order.
+constexpr int kBatch = 4;
+
+// Relaxes out-arcs a, a + step, ... < ae of a vertex settled at distance d for source s.
+__device__ __forceinline__ void relax_row(const TravParams &p, const Tile &t, int s, unsigned long long d,
+                                          long long a, long long ae, long long step) {
+    for (; a < ae; a += kBatch * step) {
+        int y[kBatch];
+        unsigned long long nd[kBatch], cur[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const long long aj = a + j * step;
+            y[j] = aj < ae ? __ldg(p.col + aj) : -1;
+            nd[j] = aj < ae ? d + __ldg(p.wt + aj) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) cur[j] = y[j] >= 0 ? p.dist[((size_t)y[j] << t.shift) + s] : 0ull;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            if (y[j] >= 0 && nd[j] < cur[j]) {
+                unsigned long long *dp = reinterpret_cast<unsigned long long *>(p.dist + ((size_t)y[j] << t.shift) + s);
+                const unsigned long long old = atomicMin(dp, nd[j]);
+                if (nd[j] < old) wenqueue(p, t, y[j], s, nd[j]);
+            }
+        }
+    }
+}
+
+// Sum of sigma_s(u) over the tight in-arcs among a, a + step, ... < ae of a
+// vertex at distance d (u at distance d - w(u, v)).
+__device__ __forceinline__ double pull_sigma(const TravParams &p, const Tile &t, int s, unsigned long long d,
+                                             long long a, long long ae, long long step, unsigned &tight) {
+    double acc = 0.0;
+    for (; a < ae; a += kBatch * step) {
+        size_t iu[kBatch];
+        unsigned long long want[kBatch];
+        bool ok[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const long long aj = a + j * step;
+            const unsigned long long w = aj < ae ? __ldg(p.rwt + aj) : ~0ull;
+            ok[j] = w <= d;
+            iu[j] = ok[j] ? ((size_t)__ldg(p.rcol + aj) << t.shift) + s : 0;
+            want[j] = d - w;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) ok[j] = ok[j] && p.dist[iu[j]] == want[j];
+        double v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) v[j] = ok[j] ? p.sigma[iu[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+            if (ok[j]) {
+                acc += v[j];
+                tight += 1;
+            }
+    }
+    return acc;
+}
+
+// Sum of c_s(y) over the tight out-arcs among a, a + step, ... < ae of a
+// vertex at distance d.
+__device__ __forceinline__ double pull_c(const TravParams &p, const Tile &t, int s, unsigned long long d, long long a,
+                                         long long ae, long long step) {
+    double acc = 0.0;
+    for (; a < ae; a += kBatch * step) {
+        size_t iy[kBatch];
+        unsigned long long want[kBatch];
+        bool ok[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+            const long long aj = a + j * step;
+            ok[j] = aj < ae;
+            iy[j] = ok[j] ? ((size_t)__ldg(p.col + aj) << t.shift) + s : 0;
+            want[j] = ok[j] ? d + __ldg(p.wt + aj) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) ok[j] = ok[j] && p.dist[iy[j]] == want[j];
+        double v[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) v[j] = ok[j] ? p.sigma[iy[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+            if (ok[j]) acc += v[j];
+    }
+    return acc;
+}
+
+// delta_s(v) from its sum of c over tight out-arcs; c_s(v) replaces sigma_s(v).
+__device__ __forceinline__ void wfinalize(const TravParams &p, const Tile &t, const uint64_t *s_need, int v, int s,
+                                          double acc) {
+    double *sp = p.sigma + ((size_t)v << t.shift) + s;
+    const double sv = *sp;
+    const double dd = sv * acc;
+    *sp = (1.0 + dd) / sv;
+    const uint64_t qm = __ldg(p.qmask + v);
+    if (qm) {
+        uint64_t y = qm & s_need[s];
+        while (y) {
+            const int q = __ffsll((long long)y) - 1;
+            y &= y - 1;
+            p.dep[s * 64 + q] = dd;
+        }
+    }
+}
+
+__device__ __forceinline__ void flag_source(const TravParams &p, int s) {
+    atomicOr(reinterpret_cast<unsigned long long *>(&p.srcflag[s >> 6]), 1ull << (s & 63));
+}
+
+// Writes the nch chunks of arcs [rb, re) (kind 0: out-arcs, 1: in-arcs) of
+// history entry e; the source slot rides in the kind field.
+__device__ __forceinline__ void emit_wchunks(const TravParams &p, long long c0, int v, int e, int s, int kind,
+                                             long long rb, long long re, int nch) {
+    const int CH = p.chunk_arcs;
+    for (int k = 0; k < nch; ++k) {
+        const long long a0 = rb + (long long)k * CH;
+        store_chunk(&p.chunks[c0 + k], v, e, k, nch, a0, (int)(min(re, a0 + CH) - a0), kind | (s << 1));
     }
 }
 
 __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
-    extern __shared__ __align__(16) double s_wacc_all[];
     const int lane = threadIdx.x & 31;
     const long long wpb = blockDim.x >> 5;
-    const long long gwarp = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
     const long long nwarps = (long long)gridDim.x * wpb;
-    double *wacc = s_wacc_all + (threadIdx.x >> 5) * WS;
-    __shared__ uint64_t s_need[WS];
-    __shared__ int32_t s_minql[WS];
-    __shared__ uint64_t s_active;
+    const long long gthr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    __shared__ uint64_t s_need[64 * kMaxWords];
+    __shared__ int32_t s_minql[64 * kMaxWords];
     __shared__ int32_t s_lstop;
-    __shared__ long long s_next;
+    __shared__ int32_t s_k;
+    Tile tl;
+    tl.S = 64 * p.nw;
+    tl.shift = 5 + __ffs(p.nw);
+    const int S = tl.S;
+    const int R = p.ring;
+    const int CH = p.chunk_arcs;
+    const long long LS = (long long)p.maxlev + 2;
+    unsigned long long *wl = p.lev_grab;
+    unsigned long long *bbase = p.bcount + R;  // consumed entries of each slot
     uint32_t gen = 0;
     WStats st;
-    const int R = p.ring;
-    const int stride = p.vs_stride;
-    const int CH = p.chunk_arcs;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_mark = timer ? global_ns() : 0ull;
     unsigned long long ns_fwd = 0, ns_bwd = 0, ns_other = 0;
-    for (int s = lane; s < WS; s += 32) wacc[s] = 0.0;
 
     for (long long tile = 0; tile < p.ntiles; ++tile) {
-        const int32_t *tsrc = p.srcs + tile * WS;
+        const int32_t *tsrc = p.srcs + tile * S;
         if (blockIdx.x == 0) {
-            const int t = threadIdx.x;
-            if (t < WS) {
+            for (int t = threadIdx.x; t < S; t += blockDim.x) {
                 const int v = tsrc[t];
                 if (v >= 0) {
-                    p.dist[(size_t)v * WS + t] = 0ull;
-                    p.sigma[(size_t)v * WS + t] = 1.0;
-                    wqueue(p, v, 0ull);
+                    p.dist[((size_t)v << tl.shift) + t] = 0ull;
+                    wenqueue(p, tl, v, t, 0ull);
                 }
             }
-            for (int i = t; i < WS * 64; i += blockDim.x) p.qlevel[i] = -1;
-            if (t == 0) p.srcflag[0] = 0ull;
+            for (int i = threadIdx.x; i < S * 64; i += blockDim.x) p.qlevel[i] = -1;
+            for (int i = threadIdx.x; i < p.nw; i += blockDim.x) p.srcflag[i] = 0ull;
         }
-        for (int s = threadIdx.x; s < WS; s += blockDim.x) {
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
             s_need[s] = v >= 0 ? p.need[v] : 0ull;
         }
@@ -117,208 +266,153 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             t_mark = t;
         }
 
-        // ---------------- forward: settle distance levels in order ----------------
-        long long d = 0, es = 0, pes = 0, pcnt = 0;
+        // ---------------- forward: settle distance values in order ----------------
+        long long d = 0, es = 0;
         int seg = 0;
+        bool first = true;
         for (;;) {
-            if (threadIdx.x == 0) {
-                long long dn = -1;
-                for (int k = 0; k < R; ++k)
-                    if (ld_vol(&p.bcount[(d + k) & (R - 1)]) > 0ull) {
-                        dn = d + k;
-                        break;
-                    }
-                s_next = dn;
+            // next slot with pending entries (every block finds the same one)
+            if (threadIdx.x == 0) s_k = R;
+            __syncthreads();
+            for (int k = threadIdx.x + (first ? 0 : 1); k < R; k += blockDim.x) {
+                const int sl = (int)((d + k) & (R - 1));
+                if (ld_vol(&p.bcount[sl]) > ld_vol(&bbase[sl])) {
+                    atomicMin(&s_k, k);
+                    break;
+                }
             }
             __syncthreads();
-            const long long dn = s_next;
+            const int kmin = s_k;
             __syncthreads();
-            if (dn < 0) break;
+            if (kmin >= R) break;
+            first = false;
             if (seg + 2 > p.maxlev) {
                 if (threadIdx.x == 0) set_err(p.ctr, kDevLevelOverflow);
                 return;
             }
-            d = dn;
+            d += kmin;
+            const unsigned long long du = (unsigned long long)d;
             const int slot = (int)(d & (R - 1));
-            const long long cnt = (long long)ld_vol(&p.bcount[slot]);
-            // settle the queued vertices whose distance for some source is d
-            for (long long i = gwarp; i < cnt; i += nwarps) {
-                const int x = p.buckets[(size_t)slot * p.bcap + i];
-                if (lane == 0) atomicAnd(&p.qbits[(size_t)x * (R >> 5) + (slot >> 5)], ~(1u << (slot & 31)));
-                const unsigned long long d0 = p.dist[(size_t)x * WS + lane];
-                const unsigned long long d1 = p.dist[(size_t)x * WS + lane + 32];
-                const unsigned b0 = __ballot_sync(kFull, d0 == (unsigned long long)d);
-                const unsigned b1 = __ballot_sync(kFull, d1 == (unsigned long long)d);
-                const uint64_t vis = p.vs[(size_t)x * stride];
-                const uint64_t F = ((uint64_t)b0 | ((uint64_t)b1 << 32)) & ~vis;
-                if (F == 0ull) continue;
-                const long long rb = p.off[x], re = p.off[x + 1];
-                const long long irb = p.roff[x], ire = p.roff[x + 1];
-                const int nout = (int)max(1ll, (re - rb + CH - 1) / CH);
-                const int nin = d > 0 ? (int)((ire - irb + CH - 1) / CH) : 0;
-                if (lane == 0) {
-                    p.vs[(size_t)x * stride] = vis | F;
-                    const long long e = es + (long long)atomicAdd(&p.lev_cnt[seg], 1ull);
-                    const long long c0 = (long long)atomicAdd(&p.lev_ccnt[seg], (unsigned long long)(nout + nin));
+            const unsigned long long b0 = ld_vol(&bbase[slot]);
+            long long cnt = (long long)(ld_vol(&p.bcount[slot]) - b0);
+            if (cnt > p.bcap) {
+                if (threadIdx.x == 0) set_err(p.ctr, kDevBucketOverflow);
+                cnt = 0;
+            }
+            const uint32_t *bk = p.buckets + (size_t)slot * p.bcap;
+            // step 1: the slot's pairs, one per lane; short rows finish here
+            {
+                ChunkGrabber grab(&wl[kGrabPairs * LS + seg], (cnt + 31) / 32, nwarps);
+                long long gi;
+                while (grab.next(gi, lane)) {
+                    const long long i = gi * 32 + lane;
+                    int x = 0, s = 0;
+                    bool ok = false;
+                    if (i < cnt) {
+                        const uint32_t pk = bk[(b0 + (unsigned long long)i) & (unsigned long long)(p.bcap - 1)];
+                        x = (int)(pk >> tl.shift);
+                        s = (int)(pk & (uint32_t)(S - 1));
+                        ok = p.dist[((size_t)x << tl.shift) + s] == du;
+                    }
+                    const unsigned am = __ballot_sync(kFull, ok);
+                    if (am == 0u) continue;
+                    unsigned long long eb = 0;
+                    if (lane == 0) eb = atomicAdd(&p.lev_cnt[seg], (unsigned long long)__popc(am));
+                    eb = __shfl_sync(kFull, eb, 0);
+                    if (!ok) continue;
+                    const long long e = es + (long long)eb + __popc(am & ((1u << lane) - 1u));
                     if (e >= p.hcap) {
                         set_err(p.ctr, kDevHistOverflow);
-                    } else if (c0 + nout + nin > p.ccap) {
-                        set_err(p.ctr, kDevChunkOverflow);
-                    } else {
-                        p.hv[e] = x;
-                        p.hm[e] = F;
-                        for (int kk = 0; kk < nout; ++kk) {
-                            const long long a0 = rb + (long long)kk * CH;
-                            store_chunk(&p.chunks[c0 + kk], x, (int)e, kk, nout, a0, (int)max(0ll, min(re, a0 + CH) - a0), 0);
-                        }
-                        for (int kk = 0; kk < nin; ++kk) {
-                            const long long a0 = irb + (long long)kk * CH;
-                            store_chunk(&p.chunks[c0 + nout + kk], x, (int)e, kk, nin, a0, (int)(min(ire, a0 + CH) - a0), 1);
-                        }
+                        continue;
                     }
-                    const unsigned pc = (unsigned)__popcll(F);
-                    st.reached += pc;
-                    st.edges += pc * (unsigned)(re - rb);
-                    if (vis == 0ull) {
+                    p.hv[e] = x;
+                    p.hs[e] = (uint16_t)s;
+                    const long long rb = __ldg(p.off + x), re = __ldg(p.off + x + 1);
+                    const long long irb = __ldg(p.roff + x), ire = d > 0 ? __ldg(p.roff + x + 1) : irb;
+                    st.reached += 1;
+                    st.edges += (unsigned)(re - rb);
+                    if (atomicCAS(&p.tag[x], -1, 0) == -1) {
                         st.vb += 1;
                         st.eb += (unsigned)(re - rb);
                     }
-                }
-                const uint64_t qm = p.qmask[x];
-                if (qm) {
-#pragma unroll
-                    for (int ii = 0; ii < 2; ++ii) {
-                        const int s = lane + 32 * ii;
-                        if ((F >> s) & 1ull) {
-                            uint64_t y = qm & s_need[s];
-                            while (y) {
-                                const int q = __ffsll((long long)y) - 1;
-                                y &= y - 1;
-                                p.qlevel[s * 64 + q] = seg;
-                            }
+                    const uint64_t qm = __ldg(p.qmask + x);
+                    if (qm) {
+                        uint64_t y = qm & s_need[s];
+                        while (y) {
+                            const int q = __ffsll((long long)y) - 1;
+                            y &= y - 1;
+                            p.qlevel[s * 64 + q] = seg;
                         }
                     }
-                }
-            }
-            // sigma of the previous level is complete: check it against 2^53
-            for (long long e = pes + gwarp; e < pes + pcnt; e += nwarps) {
-                const int v = p.hv[e];
-                const uint64_t F = p.hm[e];
-#pragma unroll
-                for (int ii = 0; ii < 2; ++ii) {
-                    const int s = lane + 32 * ii;
-                    if (((F >> s) & 1ull) && p.sigma[(size_t)v * WS + s] >= 9007199254740992.0)
-                        atomicOr((unsigned long long *)&p.srcflag[0], 1ull << s);
+                    double *sp = p.sigma + ((size_t)x << tl.shift) + s;
+                    if (re - rb <= kShortRow && ire - irb <= kShortRow) {
+                        const double sg = d > 0 ? pull_sigma(p, tl, s, du, irb, ire, 1, st.tight) : 1.0;
+                        *sp = sg;
+                        if (sg >= kTwo53) flag_source(p, s);
+                        relax_row(p, tl, s, du, rb, re, 1);
+                        st.arcs += (unsigned)((re - rb) + (ire - irb));
+                    } else {
+                        if (d == 0) *sp = 1.0;
+                        const int nin = (int)((ire - irb + CH - 1) / CH);
+                        const int nout = (int)((re - rb + CH - 1) / CH);
+                        const long long c0 =
+                            (long long)atomicAdd(&wl[kChunksF * LS + seg], (unsigned long long)(nin + nout));
+                        if (c0 + nin + nout > p.ccap) {
+                            set_err(p.ctr, kDevChunkOverflow);
+                        } else {
+                            emit_wchunks(p, c0, x, (int)e, s, 1, irb, ire, nin);
+                            emit_wchunks(p, c0 + nin, x, (int)e, s, 0, rb, re, nout);
+                        }
+                    }
                 }
             }
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             const long long ecnt = (long long)ld_vol(&p.lev_cnt[seg]);
-            const long long ccnt = (long long)ld_vol(&p.lev_ccnt[seg]);
+            const long long ccnt = (long long)ld_vol(&wl[kChunksF * LS + seg]);
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 p.lev_start[seg] = es;
                 p.lev_dist[seg] = d;
-                p.bcount[slot] = 0ull;
+                bbase[slot] = b0 + (unsigned long long)cnt;
             }
-            // relax out-arcs (kind 0) and pull sigma over in-arcs (kind 1)
-            ChunkGrabber grab(&p.lev_grab[seg], ccnt, nwarps);
-            long long c;
-            while (grab.next(c, lane)) {
-                const Chunk ch = load_chunk(&p.chunks[c]);
-                const uint64_t F = p.hm[ch.e];
-                if (ch.pad == 0) {
-                    for (int base = 0; base < ch.na; base += 32) {
-                        const long long idx = ch.a0 + base + lane;
-                        if (base + lane < ch.na) {
-                            const int w = p.col[idx];
-                            const unsigned long long nd = (unsigned long long)d + p.wt[idx];
-                            bool improved = false;
-                            uint64_t y = F;
-                            while (y) {
-                                const int s = __ffsll((long long)y) - 1;
-                                y &= y - 1;
-                                unsigned long long *dp = (unsigned long long *)&p.dist[(size_t)w * WS + s];
-                                if (nd < *dp) {
-                                    const unsigned long long old = atomicMin(dp, nd);
-                                    if (nd < old) improved = true;
-                                }
-                            }
-                            if (improved) wqueue(p, w, nd);
-                            st.arcs += 1;
+            // step 2: chunks of long rows (lanes over arcs)
+            if (ccnt > 0) {
+                ChunkGrabber grab(&wl[kGrabChunksF * LS + seg], ccnt, nwarps);
+                long long c;
+                while (grab.next(c, lane)) {
+                    const Chunk ch = load_chunk(&p.chunks[c]);
+                    const int s = ch.pad >> 1;
+                    if (ch.pad & 1) {
+                        const double part = pull_sigma(p, tl, s, du, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight);
+                        const double sum = warp_sum(part);
+                        if (lane == 0) {
+                            const double old = atomicAdd(p.sigma + ((size_t)ch.v << tl.shift) + s, sum);
+                            if (old + sum >= kTwo53) flag_source(p, s);
                         }
+                    } else {
+                        relax_row(p, tl, s, du, ch.a0 + lane, ch.a0 + ch.na, 32);
                     }
-                } else {
-                    for (int base = 0; base < ch.na; base += 32) {
-                        const long long idx = ch.a0 + base + lane;
-                        const bool valid = base + lane < ch.na;
-                        const int u = valid ? p.rcol[idx] : 0;
-                        const unsigned long long wgt = valid ? (unsigned long long)p.rwt[idx] : 0ull;
-                        if (valid) st.arcs += 1;
-                        uint64_t y = F;
-                        while (y) {
-                            const int s = __ffsll((long long)y) - 1;
-                            y &= y - 1;
-                            double val = 0.0;
-                            if (valid && wgt <= (unsigned long long)d &&
-                                p.dist[(size_t)u * WS + s] == (unsigned long long)d - wgt) {
-                                val = p.sigma[(size_t)u * WS + s];
-                                st.tight += 1;
-                            }
-                            const double sum = warp_sum(val);
-                            if (lane == 0) wacc[s] += sum;
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0) {
-                        uint64_t y = F;
-                        while (y) {
-                            const int s = __ffsll((long long)y) - 1;
-                            y &= y - 1;
-                            atomicAdd(&p.sigma[(size_t)ch.v * WS + s], wacc[s]);
-                            wacc[s] = 0.0;
-                        }
-                    }
-                    __syncwarp();
+                    if (lane < ch.na) st.arcs += (unsigned)((ch.na - lane + 31) / 32);
                 }
+                if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
-            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
-            pes = es;
-            pcnt = ecnt;
             es += ecnt;
             ++seg;
-            d += 1;
-        }
-        // the last level's sigma
-        for (long long e = pes + gwarp; e < pes + pcnt; e += nwarps) {
-            const int v = p.hv[e];
-            const uint64_t F = p.hm[e];
-#pragma unroll
-            for (int ii = 0; ii < 2; ++ii) {
-                const int s = lane + 32 * ii;
-                if (((F >> s) & 1ull) && p.sigma[(size_t)v * WS + s] >= 9007199254740992.0)
-                    atomicOr((unsigned long long *)&p.srcflag[0], 1ull << s);
-            }
         }
         const int nseg = seg;
         const long long total = es;
-        if (blockIdx.x == 0) {
-            for (int l = threadIdx.x; l <= nseg; l += blockDim.x) p.lev_ccnt[l] = 0ull;
-            if (threadIdx.x == 0) {
-                p.ctr->pslots = 0ull;
-                atomicMax(&p.ctr->levels_max, (unsigned long long)(nseg > 0 ? nseg - 1 : 0));
-            }
-        }
-        if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            atomicMax(&p.ctr->levels_max, (unsigned long long)(nseg > 0 ? nseg - 1 : 0));
         if (timer) {
             const unsigned long long t = global_ns();
             ns_fwd += t - t_mark;
             t_mark = t;
         }
 
-        // ---------------- backward (Eq. 4) over the non-empty levels ----------------
+        // ---------------- backward (Eq. 4) over the levels ----------------
         if (!(p.flags & kFlagNoBackward)) {
             if (threadIdx.x == 0) s_lstop = 0x7fffffff;
             __syncthreads();
-            for (int s = threadIdx.x; s < WS; s += blockDim.x) {
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
                 int mq = 0x7fffffff;
                 if (tsrc[s] >= 0) {
                     if (p.flags & kFlagFullBackward) {
@@ -339,136 +433,66 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             __syncthreads();
             const int lstop = s_lstop;
             for (int sg = nseg - 1; sg >= lstop && lstop < nseg; --sg) {
-                if (threadIdx.x == 0) {
-                    uint64_t a = 0;
-                    for (int b = 0; b < WS; ++b)
-                        if (s_minql[b] <= sg) a |= 1ull << b;
-                    s_active = a;
-                }
-                __syncthreads();
-                const uint64_t act = s_active;
                 const long long e0 = p.lev_start[sg];
                 const long long ne = (long long)p.lev_cnt[sg];
                 const unsigned long long dk = (unsigned long long)p.lev_dist[sg];
-                // chunks of the level's out-arcs (entries with an active source)
-                for (long long base = gwarp * 32; base < ne; base += nwarps * 32) {
-                    const long long e = e0 + base + lane;
-                    const bool valid = base + lane < ne;
-                    int v = 0, nch = 0;
-                    long long rb = 0, re = 0;
-                    if (valid && (p.hm[e] & act)) {
-                        v = p.hv[e];
-                        rb = p.off[v];
-                        re = p.off[v + 1];
-                        nch = (int)max(1ll, (re - rb + CH - 1) / CH);
-                    }
-                    int x = nch;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(kFull, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    const int tot = __shfl_sync(kFull, x, 31);
-                    unsigned long long cb = 0;
-                    if (lane == 0 && tot) cb = atomicAdd(&p.lev_ccnt[sg], (unsigned long long)tot);
-                    cb = __shfl_sync(kFull, cb, 0);
-                    if (nch) {
-                        const long long c0 = (long long)cb + (x - nch);
-                        if (c0 + nch > p.ccap) {
-                            set_err(p.ctr, kDevChunkOverflow);
+                // step 1: the level's entries, one per lane; short rows finish here
+                {
+                    ChunkGrabber grab(&wl[kGrabEntries * LS + sg], (ne + 31) / 32, nwarps);
+                    long long gi;
+                    while (grab.next(gi, lane)) {
+                        const long long i = gi * 32 + lane;
+                        if (i >= ne) continue;
+                        const long long e = e0 + i;
+                        const int s = p.hs[e];
+                        if (s_minql[s] > sg) continue;
+                        const int v = p.hv[e];
+                        const long long rb = __ldg(p.off + v), re = __ldg(p.off + v + 1);
+                        if (re - rb <= kShortRow) {
+                            const double acc = pull_c(p, tl, s, dk, rb, re, 1);
+                            wfinalize(p, tl, s_need, v, s, acc);
+                            st.arcs += (unsigned)(re - rb);
                         } else {
-                            for (int kk = 0; kk < nch; ++kk) {
-                                const long long a0 = rb + (long long)kk * CH;
-                                store_chunk(&p.chunks[c0 + kk], v, (int)e, kk, nch, a0, (int)max(0ll, min(re, a0 + CH) - a0), 0);
-                            }
-                            long long sl = -1;
-                            if (nch > 1) {
-                                const unsigned long long b = atomicAdd(&p.ctr->pslots, (unsigned long long)nch);
-                                if ((long long)(b + nch) > p.pcap)
-                                    set_err(p.ctr, kDevSlotOverflow);
-                                else
-                                    sl = (long long)b;
-                            }
-                            p.hslot[e] = sl;
+                            const int nch = (int)((re - rb + CH - 1) / CH);
+                            const long long c0 =
+                                (long long)atomicAdd(&wl[kChunksB * LS + sg], (unsigned long long)nch);
+                            if (c0 + nch > p.ccap || c0 + nch > p.pcap)
+                                set_err(p.ctr, kDevChunkOverflow);
+                            else
+                                emit_wchunks(p, c0, v, (int)e, s, 0, rb, re, nch);
                         }
                     }
                 }
                 if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
-                const long long ccnt = (long long)ld_vol(&p.lev_ccnt[sg]);
-                ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + sg], ccnt, nwarps);
-                long long c;
-                while (grab.next(c, lane)) {
-                    const Chunk ch = load_chunk(&p.chunks[c]);
-                    const uint64_t F = p.hm[ch.e] & act;
-                    for (int base = 0; base < ch.na; base += 32) {
-                        const long long idx = ch.a0 + base + lane;
-                        const bool valid = base + lane < ch.na;
-                        const int w = valid ? p.col[idx] : 0;
-                        const unsigned long long nd = valid ? dk + p.wt[idx] : 0ull;
-                        if (valid) st.arcs += 1;
-                        uint64_t y = F;
-                        while (y) {
-                            const int s = __ffsll((long long)y) - 1;
-                            y &= y - 1;
-                            double val = 0.0;
-                            if (valid && p.dist[(size_t)w * WS + s] == nd) val = p.sigma[(size_t)w * WS + s];
-                            const double sum = warp_sum(val);
-                            if (lane == 0) wacc[s] += sum;
-                        }
-                    }
-                    __syncwarp();
-                    const long long slot0 = ch.nch > 1 ? p.hslot[ch.e] : -1;
-                    bool finalize = ch.nch == 1;
-                    if (ch.nch > 1) {
-                        double *prow = p.partial + (size_t)(slot0 + ch.k) * WS;
-                        for (int s = lane; s < WS; s += 32) {
-                            __stcg(&prow[s], wacc[s]);
-                            wacc[s] = 0.0;
-                        }
-                        __threadfence();
-                        __syncwarp();
-                        int prev = 0;
-                        if (lane == 0) prev = atomicAdd(&p.pdone[slot0], 1);
-                        prev = __shfl_sync(kFull, prev, 0);
-                        if (prev == ch.nch - 1) {
+                const long long ccnt = (long long)ld_vol(&wl[kChunksB * LS + sg]);
+                // step 2: chunks of long rows (partial sums indexed by chunk;
+                // an entry's chunks are consecutive); the last chunk of an
+                // entry to finish combines them in chunk order
+                if (ccnt > 0) {
+                    ChunkGrabber grab(&wl[kGrabChunksB * LS + sg], ccnt, nwarps);
+                    long long c;
+                    while (grab.next(c, lane)) {
+                        const Chunk ch = load_chunk(&p.chunks[c]);
+                        const int s = ch.pad >> 1;
+                        const double part = pull_c(p, tl, s, dk, ch.a0 + lane, ch.a0 + ch.na, 32);
+                        const double sum = warp_sum(part);
+                        if (lane < ch.na) st.arcs += (unsigned)((ch.na - lane + 31) / 32);
+                        if (lane == 0) {
+                            const long long base = c - ch.k;
+                            __stcg(&p.partial[c], sum);
                             __threadfence();
-                            for (int s = lane; s < WS; s += 32) {
-                                double a = 0.0;
-                                for (int kk = 0; kk < ch.nch; ++kk) a += __ldcg(&p.partial[(size_t)(slot0 + kk) * WS + s]);
-                                wacc[s] = a;
-                            }
-                            if (lane == 0) p.pdone[slot0] = 0;
-                            finalize = true;
-                        }
-                        __syncwarp();
-                    }
-                    if (finalize) {
-                        const uint64_t qm = p.qmask[ch.v];
-                        double *row = p.sigma + (size_t)ch.v * WS;
-#pragma unroll
-                        for (int ii = 0; ii < 2; ++ii) {
-                            const int s = lane + 32 * ii;
-                            if ((F >> s) & 1ull) {
-                                const double sv = row[s];
-                                const double dd = sv * wacc[s];
-                                row[s] = (1.0 + dd) / sv;
-                                if (qm) {
-                                    uint64_t y = qm & s_need[s];
-                                    while (y) {
-                                        const int q = __ffsll((long long)y) - 1;
-                                        y &= y - 1;
-                                        p.dep[s * 64 + q] = dd;
-                                    }
-                                }
+                            const int prev = atomicAdd(&p.pdone[base], 1);
+                            if (prev == ch.nch - 1) {
+                                __threadfence();
+                                double acc = 0.0;
+                                for (int k = 0; k < ch.nch; ++k) acc += __ldcg(&p.partial[base + k]);
+                                p.pdone[base] = 0;
+                                wfinalize(p, tl, s_need, ch.v, s, acc);
                             }
                         }
-                        __syncwarp();
-                        for (int s = lane; s < WS; s += 32) wacc[s] = 0.0;
                     }
-                    __syncwarp();
+                    if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
                 }
-                if (blockIdx.x == 0 && threadIdx.x == 0) p.ctr->pslots = 0ull;
-                if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
         }
         if (timer) {
@@ -484,42 +508,36 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             const bool exact = (p.exact_q >> q) & 1ull;
             double sum = 0.0;
             bool flagged = false;
-            for (int s = 0; s < WS; ++s) {
+            for (int s = 0; s < S; ++s) {
                 if (tsrc[s] < 0) continue;
                 double mlt = 0.0;
                 if (exact)
                     mlt = ((s_need[s] >> q) & 1ull) ? 1.0 : 0.0;
                 else if (p.mult)
-                    mlt = (double)p.mult[((size_t)tile * WS + s) * 64 + q];
+                    mlt = (double)p.mult[((size_t)tile * S + s) * 64 + q];
                 if (mlt != 0.0) {
                     sum += mlt * p.dep[s * 64 + q];
-                    if ((p.srcflag[0] >> s) & 1ull) flagged = true;
+                    if ((p.srcflag[s >> 6] >> (s & 63)) & 1ull) flagged = true;
                 }
             }
             p.tile_partial[tile * 64 + q] = sum;
             if (flagged) p.qflags[q] |= 1u;
         }
         if (!(p.flags & kFlagNoReset)) {
-            for (long long e = gwarp; e < total; e += nwarps) {
+            for (long long e = gthr; e < total; e += nthr) {
                 const int v = p.hv[e];
-                const uint64_t F = p.hm[e];
-#pragma unroll
-                for (int ii = 0; ii < 2; ++ii) {
-                    const int s = lane + 32 * ii;
-                    if ((F >> s) & 1ull) {
-                        p.sigma[(size_t)v * WS + s] = 0.0;
-                        p.dist[(size_t)v * WS + s] = ~0ull;
-                    }
-                }
-                if (lane == 0) p.vs[(size_t)v * stride] = 0ull;
+                const size_t iv = ((size_t)v << tl.shift) + p.hs[e];
+                p.sigma[iv] = 0.0;
+                p.dist[iv] = ~0ull;
+                p.tag[v] = -1;
             }
             if (blockIdx.x == 0) {
                 for (int l = threadIdx.x; l <= nseg + 1; l += blockDim.x) {
                     p.lev_cnt[l] = 0ull;
-                    p.lev_ccnt[l] = 0ull;
-                    p.lev_grab[l] = 0ull;
-                    p.lev_grab[p.maxlev + 2 + l] = 0ull;
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) wl[k * LS + l] = 0ull;
                 }
+                for (int i = threadIdx.x; i < 2 * R; i += blockDim.x) p.bcount[i] = 0ull;
             }
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
@@ -540,14 +558,12 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
 
 bc_status launch_weighted(bc_graph *g, TravParams &p) {
     const int threads = g->block_threads;
-    const size_t smem = (size_t)(threads / 32) * WS * sizeof(double);
-    BCD_CUDA(cudaFuncSetAttribute((const void *)wtrav_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wtrav_kernel, threads, smem));
+    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wtrav_kernel, threads, 0));
     if (per_sm < 1) return set_error(BC_E_INTERNAL, "weighted traversal kernel cannot be resident");
     dim3 grid((unsigned)(g->num_sms * per_sm)), block((unsigned)threads);
     void *args[] = {(void *)&p};
-    BCD_CUDA(cudaLaunchCooperativeKernel((const void *)wtrav_kernel, grid, block, args, smem, g->stream));
+    BCD_CUDA(cudaLaunchCooperativeKernel((const void *)wtrav_kernel, grid, block, args, 0, g->stream));
     g->launches += 1;
     g->last_grid = (int)grid.x;
     return BC_OK;

@@ -295,10 +295,14 @@ def wer():
     return [(x, O.Graph.from_csr(x)) for x in (g255, g3)]
 
 
+WCFGS = [{}, {"weighted_words": 1}, {"weighted_words": 4, "chunk_arcs": 32}]
+
+
+@pytest.mark.parametrize("cfg", WCFGS)
 @pytest.mark.parametrize("which", [0, 1])
-def test_weighted_probe_dist_sigma_delta(bcd, wer, which):
+def test_weighted_probe_dist_sigma_delta(bcd, wer, which, cfg):
     g, og = wer[which]
-    dg = make(bcd, g)
+    dg = make(bcd, g, **cfg)
     srcs = np.array(sorted(set(gg.random_vertices(g.n, 30, 5).tolist())), dtype=np.int32)
     tgts = np.array(list(dict.fromkeys(gg.random_vertices(g.n, 12, 6).tolist())), dtype=np.int32)
     dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, tgts)
@@ -311,10 +315,13 @@ def test_weighted_probe_dist_sigma_delta(bcd, wer, which):
                 assert close(dep[i, j], st["delta"][t]), (s, t, dep[i, j], st["delta"][t])
 
 
+@pytest.mark.parametrize("cfg", WCFGS)
 @pytest.mark.parametrize("which", [0, 1])
-def test_weighted_exact_and_batch(bcd, wer, which):
+def test_weighted_exact_and_batch(bcd, wer, which, cfg):
+    """Batches over several tiles (64-source tiles) with a ragged last tile,
+    and one wide tile; long rows split into 32-arc chunks."""
     g, og = wer[which]
-    dg = make(bcd, g)
+    dg = make(bcd, g, **cfg)
     qs = gg.random_vertices(g.n, 12, 104).tolist()
     out, _ = bcd.bc_batch(dg, [{"r": r} for r in qs])
     for r, o in zip(qs, out):
@@ -339,12 +346,14 @@ def test_weighted_closed_forms_and_sampling(bcd, wer):
         assert info["rv_size"] == k and close(got, want)
 
 
-def test_weighted_rmat_small(bcd):
-    """A small weighted R-MAT (the weighted configuration at scale 12)."""
+@pytest.mark.parametrize("cfg", [{}, {"weighted_words": 2, "chunk_arcs": 64}])
+def test_weighted_rmat_small(bcd, cfg):
+    """A small weighted R-MAT (the weighted configuration at scale 12): hub
+    rows of hundreds of arcs go through the chunked path."""
     g = gg.rmat(12, 8, seed=12)
     g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     og = O.Graph.from_csr(g)
-    dg = make(bcd, g)
+    dg = make(bcd, g, **cfg)
     qs = gg.random_vertices(g.n, 8, 104).tolist() + gg.top_inout_vertices(g, 2).tolist()
     out, _ = bcd.bc_batch(dg, [{"r": r} for r in qs])
     for r, o in zip(qs, out):

@@ -7,6 +7,11 @@ every query within 1e-9; full BC(r) for the queries the oracle can finish.
 R-MAT scale 22 with 30 % reciprocal arcs (the sampled batch): the draws of
 eps = 0.01, delta = 0.1, seed 7 bit-exact, and the dependencies of drawn
 sources within 1e-9.
+The R-MAT scale 20 graph with weights uniform in [1, 255] (seed 3; the
+weighted batch of 32 uniform queries, seed 104), in the default weighted tile
+width: RV lists bit-exact, uint64 distances and sigma of sampled sources
+bit-exact and their dependencies on all 32 queries within 1e-9, and the
+queries with empty RV answered 0.
 """
 import numpy as np
 import pytest
@@ -116,3 +121,51 @@ def test_rmat22_sampled_draws_and_dependencies(bcd, rmat22):
                 assert close(dep[i, 0], odep[i, 0]), (int(srcs[i]), dep[i, 0], odep[i, 0])
             checked += 1
     assert checked == 1
+
+
+@pytest.fixture(scope="module")
+def rmat20w(bcd):
+    g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    qs = [int(x) for x in gg.random_vertices(g.n, 32, 104)]
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    return g, O.Graph.from_csr(g), dg, qs
+
+
+def test_rmat20_weighted_rv_lists(bcd, rmat20w):
+    g, og, dg, qs = rmat20w
+    for r in dict.fromkeys(qs):
+        assert np.array_equal(bcd.bc_rv_compute(dg, r), O.rv(og, r)), r
+
+
+def test_rmat20_weighted_sampled_sources(bcd, rmat20w):
+    g, og, dg, qs = rmat20w
+    assert bcd.bc_get_config(dg)["weighted_words"] == 16
+    sizes = {r: bcd.bc_rv_compute(dg, r).shape[0] for r in dict.fromkeys(qs)}
+    big = max(sizes, key=sizes.get)
+    union = O.rv(og, big)
+    rng = np.random.default_rng(6)
+    srcs = np.sort(rng.choice(union, size=12, replace=False)).astype(np.int32)
+    qv = np.array(list(dict.fromkeys(qs)), dtype=np.int32)
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, qv)
+    odep, ofl, _ = O.dependencies(og, srcs, qv, 0)
+    for i, s in enumerate(srcs.tolist()):
+        st = O.source_state(og, s)
+        assert np.array_equal(dist[i], st["dist"]), s
+        if not st["flags"]:
+            assert np.array_equal(sig[i], st["sigma"]), s
+        for j in range(qv.shape[0]):
+            if qv[j] != s:
+                assert close(dep[i, j], odep[i, j]), (s, int(qv[j]), dep[i, j], odep[i, j])
+
+
+def test_rmat20_weighted_empty_rv_queries(bcd, rmat20w):
+    """The queries outside the giant component have no in-arcs here: RV is
+    empty and BC(r) = 0 (Prop. 1); the oracle agrees on each."""
+    g, og, dg, qs = rmat20w
+    empty = [r for r in dict.fromkeys(qs) if bcd.bc_rv_compute(dg, r).shape[0] == 0]
+    assert len(empty) >= 10
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in empty])
+    for r, o in zip(empty, out):
+        want, k, _ = O.bc_exact(og, r, 0)
+        assert o["status"] == 0 and o["rv_size"] == k == 0 and o["bc"] == want == 0.0, (r, o)
