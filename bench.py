@@ -459,6 +459,26 @@ def run_profile_case(args):
     dg.close()
 
 
+def run_wprofile_case(args):
+    """A small launch of the weighted traversal kernel for ncu captures: one
+    sampled query (T = args.case_T draws, seed 7) on the vertex of largest
+    in-degree x out-degree of R-MAT scale args.case_scale (edge factor 16,
+    seed 20) with weights uniform in [1, 255] (seed 3)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_08739_gb300 as bcd
+    g = gg.rmat(args.case_scale, 16, 0.57, 0.19, 0.19, seed=20)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    if args.weighted_words:
+        bcd.bc_set_config(dg, weighted_words=args.weighted_words)
+    r = int(gg.top_inout_vertices(g, 1)[0])
+    out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
+    print(json.dumps({"case": "wprofile", "scale": args.case_scale, "r": r, "T": args.case_T, "bc": out[0]["bc"],
+                      "config": bcd.bc_get_config(dg), "info": info}), flush=True)
+    dg.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,8 +488,11 @@ def main():
     ap.add_argument("--tile-words", type=int, default=2)
     ap.add_argument("--cpu-sources", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="", choices=["", "profile"],
-                    help="profile: one small sampled batch (for ncu), no JSON bench line")
+    ap.add_argument("--case", default="", choices=["", "profile", "wprofile"],
+                    help="profile / wprofile: one small sampled batch on the unweighted / weighted R-MAT (for ncu), "
+                         "no JSON bench line")
+    ap.add_argument("--case-scale", type=int, default=20, help="R-MAT scale of the wprofile case")
+    ap.add_argument("--weighted-words", type=int, default=0, help="weighted tile width (64-source words; 0: default)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--case-T", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
@@ -483,6 +506,8 @@ def main():
         run_serve(args)
     elif args.case == "profile":
         run_profile_case(args)
+    elif args.case == "wprofile":
+        run_wprofile_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -275,7 +275,7 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
     g->launches += 5;
     if (g->weighted) {
         // widest weighted tile (up to 1024 sources) whose per-pair state
-        // (dist, sigma, history, bucket share: about 32 bytes) fits in half of
+        // (dist, sigma, history, bucket share: about 40 bytes) fits in half of
         // the free device memory, with vertex << log2(S) in 32 bits
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -284,7 +284,7 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
         }
         int nw = 16;
         while (nw > 1 && ((((uint64_t)d->n) << 6) * (uint64_t)nw > (1ull << 32) ||
-                          (double)d->n * 64.0 * nw * 32.0 > 0.5 * (double)fr))
+                          (double)d->n * 64.0 * nw * 40.0 > 0.5 * (double)fr))
             nw >>= 1;
         g->weighted_words = nw;
     }

@@ -238,8 +238,11 @@ bc_status ensure_weighted_state(bc_graph *g) {
     ws.ring = R;
     const size_t n = (size_t)g->n;
     const size_t S = 64 * (size_t)ws.W;
+    // pending pairs of one distance: a few times the average pairs per
+    // distance value (the pairs of a tile spread over hundreds of distances,
+    // stale entries included); grown on overflow
     int64_t bcap = 1 << 14;
-    while ((size_t)bcap * 256 < n * S) bcap *= 2;
+    while ((size_t)bcap * 64 < n * S) bcap *= 2;
     ws.bcap = bcap;
     BCD_TRY(dev_alloc(&ws.dist, n * S));
     BCD_TRY(dev_alloc(&ws.buckets, (size_t)R * (size_t)bcap));
