@@ -479,6 +479,55 @@ def run_wprofile_case(args):
     dg.close()
 
 
+def run_set_experiment(args):
+    """The set experiment of Section 5 (Table 6) on the R-MAT 20 graph: for
+    random sets of 5, 10 and 15 vertices, BCD with tau = 1000 (HYBRID: exact
+    when |RV(r)| <= 1000, else 1000 draws, seed 7) as one batch; errors
+    against the exact scores (exact path, one batch over all set vertices),
+    the batch's time and its RV time, |RV| statistics, and the same set run
+    one query at a time."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    import paper_1708_08739_gb300 as bcd
+    g, _, _ = make_workload()
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    sets = {k: [int(x) for x in gg.random_vertices(g.n, k, 200 + k)] for k in (5, 10, 15)}
+    every = list(dict.fromkeys(v for vs in sets.values() for v in vs))
+    t = time.time()
+    ex, exi = bcd.bc_batch(dg, [{"r": r} for r in every])
+    t_exact = time.time() - t
+    exact = {r: o["bc"] for r, o in zip(every, ex)}
+    log("set experiment: exact scores of %d vertices in %.1f s" % (len(every), t_exact))
+    tau = 1000
+    rows = []
+    for k, vs in sets.items():
+        specs = [{"r": r, "kind": bcd.BC_QUERY_HYBRID, "T": tau, "seed": 7} for r in vs]
+        bcd.bc_batch(dg, specs)  # warm
+        torch.cuda.synchronize()
+        t = time.time()
+        out, info = bcd.bc_batch(dg, specs)
+        t_set = time.time() - t
+        t = time.time()
+        for sp in specs:
+            bcd.bc_batch(dg, [sp])
+        t_one = time.time() - t
+        err = []
+        for r, o in zip(vs, out):
+            e = exact[r]
+            err.append(0.0 if e == o["bc"] else 100.0 * abs(o["bc"] - e) / abs(e))
+        rv = [o["rv_size"] for o in out]
+        rows.append({"set_size": k, "error_pct": {"avg": sum(err) / k, "max": max(err), "min": min(err)},
+                     "time_s": t_set, "time_rv_s": info["ms_rv"] / 1000.0,
+                     "rv_size": {"avg": sum(rv) / k, "max": max(rv), "min": min(rv)},
+                     "exact_queries": sum(1 for x in rv if x <= tau), "sources_run": info["sources_run"],
+                     "one_at_a_time_s": t_one})
+    print(json.dumps({"experiment": "set", "graph": WORKLOADS[WORKLOAD].split(";")[0], "tau": tau,
+                      "exact_reference_s": t_exact, "rows": rows}), flush=True)
+    dg.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,6 +545,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--case-T", type=int, default=512)
     ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
+    ap.add_argument("--set-experiment", action="store_true",
+                    help="the set experiment of Section 5 (sets of 5, 10, 15 vertices, tau = 1000)")
     ap.add_argument("--serve-queries", type=int, default=256)
     ap.add_argument("--serve-rv-max", type=int, default=100000)
     args = ap.parse_args()
@@ -504,6 +555,8 @@ def main():
         args.warmup = 3
     if args.serve:
         run_serve(args)
+    elif args.set_experiment:
+        run_set_experiment(args)
     elif args.case == "profile":
         run_profile_case(args)
     elif args.case == "wprofile":
