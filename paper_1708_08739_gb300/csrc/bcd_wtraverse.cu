@@ -300,6 +300,13 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                 cnt = 0;
             }
             const uint32_t *bk = p.buckets + (size_t)slot * p.bcap;
+            // the level's start and distance are recorded before the barrier
+            // that ends step 1: the backward pass may follow the last level
+            // with no other barrier in between
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                p.lev_start[seg] = es;
+                p.lev_dist[seg] = d;
+            }
             // step 1: the slot's pairs, one per lane; short rows finish here
             {
                 ChunkGrabber grab(&wl[kGrabPairs * LS + seg], (cnt + 31) / 32, nwarps);
@@ -369,11 +376,9 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             const long long ecnt = (long long)ld_vol(&p.lev_cnt[seg]);
             const long long ccnt = (long long)ld_vol(&wl[kChunksF * LS + seg]);
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                p.lev_start[seg] = es;
-                p.lev_dist[seg] = d;
-                bbase[slot] = b0 + (unsigned long long)cnt;
-            }
+            // every block has read the slot's base by now; the new base is
+            // next read R distances later, many barriers on
+            if (blockIdx.x == 0 && threadIdx.x == 0) bbase[slot] = b0 + (unsigned long long)cnt;
             // step 2: chunks of long rows (lanes over arcs)
             if (ccnt > 0) {
                 ChunkGrabber grab(&wl[kGrabChunksF * LS + seg], ccnt, nwarps);

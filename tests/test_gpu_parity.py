@@ -331,6 +331,21 @@ def test_weighted_exact_and_batch(bcd, wer, which, cfg):
         assert close(o["bc"], want) and close(single, want), (r, o["bc"], single, want)
 
 
+def test_weighted_repeated_multitile(bcd, wer):
+    """Many launches of ten 64-source tiles (weights 1..3: many ties and
+    distance levels): every result must match, run after run. Guards the
+    ordering between the last forward level and the backward pass."""
+    g, og = wer[1]
+    qs = gg.random_vertices(g.n, 6, 104).tolist()
+    want = {r: O.bc_exact(og, r, 0)[0] for r in qs}
+    for it in range(6):
+        dg = make(bcd, g, weighted_words=1, block_threads=(512, 256, 128)[it % 3])
+        for r in qs:
+            got, _ = bcd.bc_exact(dg, r)
+            assert close(got, want[r]), (it, r, got, want[r])
+        dg.close()
+
+
 def test_weighted_closed_forms_and_sampling(bcd, wer):
     wt = csr(3, [(0, 1), (0, 2), (2, 1)], [2, 1, 1])
     dg = make(bcd, wt)
