@@ -82,6 +82,7 @@ struct TravParams {
     int32_t pad0;
     int32_t *tag;       // [n] last level a vertex was appended at, -1 none
     double *sigma;      // [n * S] sigma, then c = (1 + delta) / sigma in place
+    double *acc;        // [n * S] backward sums of c over tight out-arcs (unweighted), zero between levels
     // level history
     int32_t *hv;        // [hcap]
     uint64_t *hm;       // [hcap * W] (unweighted)
@@ -147,6 +148,7 @@ struct bcd_workspace {
     int vs_stride = 0;
     int32_t *tag = nullptr;
     double *sigma = nullptr;
+    double *acc = nullptr;        // [n * 64 * W] unweighted graphs
     // history
     int32_t *hv = nullptr;
     uint64_t *hm = nullptr;

@@ -165,8 +165,8 @@ __global__ void reduce_tiles(const double *tile_partial, int64_t ntiles, const d
 // ---------------------------------------------------------------------------
 
 // Level history and chunk lists. Unweighted entries carry a W-word source
-// mask and chunked rows a partial-row slot; weighted entries carry one source
-// slot, and the partial sums of their long rows are indexed by chunk. On a
+// mask; weighted entries carry one source slot, and the backward partial sums
+// of their long rows are indexed by chunk (pcap = ccap). On a
 // weighted graph the masks serve only the one-word reach traversals (RV and
 // the tile order), which get their own, smaller capacity hmcap.
 static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t pcap, int64_t hmcap) {
@@ -189,11 +189,11 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     BCD_TRY(dev_alloc(&ws.hv, (size_t)hcap));
     BCD_TRY(dev_alloc(&ws.hm, wg ? (size_t)hmcap : (size_t)hcap * ws.W));
     BCD_TRY(dev_alloc(&ws.hs, wg ? (size_t)hcap : (size_t)1));
-    BCD_TRY(dev_alloc(&ws.hslot, wg ? (size_t)1 : (size_t)hcap));
+    BCD_TRY(dev_alloc(&ws.hslot, (size_t)1));
     BCD_TRY(dev_alloc(&ws.chunks, (size_t)ccap));
-    BCD_TRY(dev_alloc(&ws.partial, wg ? (size_t)pcap : (size_t)pcap * 64 * ws.W));
-    BCD_TRY(dev_alloc(&ws.pdone, (size_t)pcap));
-    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)pcap, g->stream));
+    BCD_TRY(dev_alloc(&ws.partial, wg ? (size_t)pcap : (size_t)1));
+    BCD_TRY(dev_alloc(&ws.pdone, wg ? (size_t)pcap : (size_t)1));
+    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)(wg ? pcap : 1), g->stream));
     return BC_OK;
 }
 
@@ -281,6 +281,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.vs);
     dev_free(ws.tag);
     dev_free(ws.sigma);
+    dev_free(ws.acc);
     dev_free(ws.hv);
     dev_free(ws.hm);
     dev_free(ws.hs);
@@ -332,6 +333,7 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.vs, (size_t)n * ws.vs_stride));
     BCD_TRY(dev_alloc(&ws.tag, (size_t)n));
     BCD_TRY(dev_alloc(&ws.sigma, (size_t)n * 64 * W));
+    BCD_TRY(dev_alloc(&ws.acc, g->weighted ? (size_t)1 : (size_t)n * 64 * W));
     const int64_t ch = g->chunk_arcs;
     BCD_TRY(alloc_history(g, 8 * n + 4096, 8 * n + 8 * (m / ch) + 4096, 8 * (m / ch) + 4096, 16 * n + 4096));
     BCD_TRY(alloc_levels(g, std::min<int64_t>(g->weighted ? std::max<int64_t>(n + 1, 65536) : n + 1,

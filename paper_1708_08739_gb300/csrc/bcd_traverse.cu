@@ -14,9 +14,12 @@
 //   backward (Eq. 4): levels from the deepest one up to the shallowest level
 //            any query vertex sits at. With c_s(w) = (1 + delta_s(w)) /
 //            sigma_s(w), delta_s(v) = sigma_s(v) * sum over tight out-arcs
-//            (v, w) of c_s(w), a pull over out-arcs in CSR order. Long rows
-//            are split into chunks whose partial sums are combined in chunk
-//            order, so the result does not depend on scheduling.
+//            (v, w) of c_s(w). The sum is pushed: the entries of level L + 1
+//            add c_s(w) along their tight in-arcs (R(G), in chunks) into an
+//            accumulator slab acc[v][s] with fp64 atomic adds, which do not
+//            hold the warp; after a barrier the level-L entries turn acc
+//            into delta and c. The sum order follows the schedule, so delta
+//            can differ from run to run in its last bits.
 // Reach mode (RV(r), Section 4.1) runs the forward pass only, over R(G),
 // with one source slot per query root, and ORs every level mask into rvmask.
 //
@@ -66,17 +69,6 @@ __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app
         } else {
             p.hv[e] = wv;
             emit_chunks(p, c0, wv, (int)e, wnch, wrb, wre);
-            if (MODE == kModeSpd) {
-                long long sl = -1;
-                if (wnch > 1) {
-                    const unsigned long long b = atomicAdd(&p.ctr->pslots, (unsigned long long)wnch);
-                    if ((long long)(b + wnch) > p.pcap)
-                        set_err(p.ctr, kDevSlotOverflow);
-                    else
-                        sl = (long long)b;
-                }
-                p.hslot[e] = sl;
-            }
         }
     }
 }
@@ -128,18 +120,7 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
                 atomicAdd(&p.ctr->vb, 1ull);
                 atomicAdd(&p.ctr->eb, (unsigned long long)(re - rb));
             }
-            if (MODE == kModeSpd) {
-                p.sigma[(size_t)v * S + t] = 1.0;
-                long long sl = -1;
-                if (nch > 1) {
-                    const unsigned long long b = atomicAdd(&p.ctr->pslots, (unsigned long long)nch);
-                    if ((long long)(b + nch) > p.pcap)
-                        set_err(p.ctr, kDevSlotOverflow);
-                    else
-                        sl = (long long)b;
-                }
-                p.hslot[t] = sl;
-            }
+            if (MODE == kModeSpd) p.sigma[(size_t)v * S + t] = 1.0;
         }
     }
     if (MODE == kModeSpd) {
@@ -323,195 +304,217 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
     }
 }
 
-// delta for the (v, F) entry once its sum of c over tight out-arcs is known.
-// Lane l holds the source pairs (64 k + 2 l, 64 k + 2 l + 1), k < W.
+// Eq. 4, push form, for level L: the entries of level L + 1 send
+// c_s(w) = (1 + delta_s(w)) / sigma_s(w) back along their in-arcs (v, w) that
+// are tight for an active source s (v at level L for s), adding it to the
+// accumulator acc_s(v) with fp64 atomic adds. The in-arc chunks of level
+// L + 1 were cut in the previous step. Lane l holds sources l + 32 i, as in
+// the forward pass; two tight tails are handled per step.
 template <int W>
-__device__ __forceinline__ void finalize_entry(const TravParams &p, int v, const uint64_t (&F)[W],
-                                               const double (&acc)[2 * W], const uint64_t *s_need, int lane) {
+__device__ void push_level(const TravParams &p, int L, long long ccnt, const uint64_t *s_act, long long nwarps,
+                           Stats &st) {
     constexpr int S = 64 * W;
-    const uint64_t qm = p.qmask[v];
-    double *row = p.sigma + (size_t)v * S;
+    constexpr int PL = 2 * W;
+    const int lane = threadIdx.x & 31;
+    const int cur = 1 + (L & 1);  // parity slot holding the level-L masks
+    const int stride = p.vs_stride;
+    ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + L], ccnt, nwarps);
+    long long c;
+    while (grab.next(c, lane)) {
+        const Chunk ch = load_chunk(&p.chunks[c]);
+        const int w = ch.v;
+        const long long a0 = ch.a0;
+        const int na = ch.na;
+        int vnext = lane < na ? p.rcol[a0 + lane] : 0;
+        uint64_t F[W];
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
+        for (int k = 0; k < W; ++k) F[k] = p.hm[(size_t)ch.e * W + k] & s_act[k];
+        double cw[PL];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int s = 64 * k + 2 * lane + j;
-            if ((F[k] >> (2 * lane + j)) & 1ull) {
-                const double sv = row[s];
-                const double d = sv * acc[2 * k + j];
-                row[s] = (1.0 + d) / sv;
-                if (qm) {
-                    uint64_t x = qm & s_need[s];
-                    while (x) {
-                        const int q = __ffsll((long long)x) - 1;
-                        x &= x - 1;
-                        p.dep[s * 64 + q] = d;
-                    }
+        for (int ii = 0; ii < PL; ++ii) cw[ii] = p.sigma[(size_t)w * S + lane + 32 * ii];
+        for (int base = 0; base < na; base += 32) {
+            const bool valid = base + lane < na;
+            const int v = vnext;
+            vnext = base + 32 + lane < na ? p.rcol[a0 + base + 32 + lane] : 0;
+            uint64_t tm[W];
+            bool any = false;
+            if (valid) {
+                const uint64_t *row = p.vs + (size_t)v * stride;
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    tm[k] = F[k] & row[cur * W + k];
+                    any |= tm[k] != 0ull;
+                }
+                st.arcs += 1;
+            } else {
+#pragma unroll
+                for (int k = 0; k < W; ++k) tm[k] = 0ull;
+            }
+            unsigned bal = __ballot_sync(kFull, any);
+            while (bal) {
+                const int i0 = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int i1 = bal ? __ffs(bal) - 1 : -1;
+                if (bal) bal &= bal - 1;
+                const int j1 = i1 < 0 ? i0 : i1;
+                const int v0 = __shfl_sync(kFull, v, i0);
+                const int v1 = __shfl_sync(kFull, v, j1);
+                uint64_t n0[W], n1[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    n0[k] = __shfl_sync(kFull, tm[k], i0);
+                    n1[k] = i1 < 0 ? 0ull : __shfl_sync(kFull, tm[k], j1);
+                }
+                double *r0 = p.acc + (size_t)v0 * S;
+                double *r1 = p.acc + (size_t)v1 * S;
+#pragma unroll
+                for (int ii = 0; ii < PL; ++ii) {
+                    const int s = lane + 32 * ii;
+                    if (mask_bit<W>(n0, s)) atomicAdd(&r0[s], cw[ii]);
+                    if (mask_bit<W>(n1, s)) atomicAdd(&r1[s], cw[ii]);
                 }
             }
         }
     }
 }
 
-// Eq. 4 for the entries of level L (backward pass). For the tight heads of a
-// group of 32 arcs, only the 16-byte source pairs that hold a tight source
-// are copied (cp.async, L2) into the warp's shared-memory stage, packed head
-// after head, so that one round trip brings in a whole group; the sums then
-// run over the heads in arc order.
+// Second phase of a backward step: delta and c for the entries of level L
+// (their accumulators are complete), then, when the pass goes on to level
+// L - 1, the in-arc chunks of level L (entries with a source active at
+// L - 1) and the parity masks of level L - 1 (in the slot that held level
+// L + 1). Lane l holds the source pairs (64 k + 2 l, 64 k + 2 l + 1).
 template <int W>
-__device__ void backward_level(const TravParams &p, int L, long long cs, long long ccnt,
-                               const uint64_t *s_active, const uint64_t *s_need, long long gwarp,
-                               long long nwarps, double *stage, Stats &st) {
+__device__ void settle_level(const TravParams &p, int L, int Lmax, bool next, const uint64_t *s_act,
+                             const uint64_t *s_act_next, const uint64_t *s_need, long long gwarp, long long nwarps,
+                             long long gthr, long long nthr) {
     constexpr int S = 64 * W;
-    constexpr int PL = 2 * W;
-    constexpr int KU = kStageBytes / 16;  // 16-byte units the stage holds
-    constexpr unsigned long long kEven = 0x5555555555555555ull;
     const int lane = threadIdx.x & 31;
-    const int nx = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
-    const unsigned long long below = (lane == 0) ? 0ull : (~0ull >> (64 - 2 * lane));  // bits of pairs < lane
-    ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + L], ccnt, nwarps);
-    long long c;
-    while (grab.next(c, lane)) {
-        const Chunk ch = load_chunk(&p.chunks[cs + c]);
-        const int v = ch.v, e = ch.e, k = ch.k, nch = ch.nch;
-        const long long a0 = ch.a0;
-        const int na = ch.na;
-        int wv_next = lane < na ? p.col[a0 + lane] : 0;
+    const long long e0 = p.lev_start[L], e1 = e0 + (long long)p.lev_cnt[L];
+    for (long long e = e0 + gwarp; e < e1; e += nwarps) {
         uint64_t F[W];
-        bool anyF = false;
+        bool any = false;
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            F[w] = p.hm[(size_t)e * W + w] & s_active[w];
-            anyF |= F[w] != 0ull;
+        for (int k = 0; k < W; ++k) {
+            F[k] = p.hm[(size_t)e * W + k] & s_act[k];
+            any |= F[k] != 0ull;
         }
-        if (!anyF) continue;
-        double acc[PL];
+        if (!any) continue;
+        const int v = p.hv[e];
+        const uint64_t qm = p.qmask[v];
+        double *srow = p.sigma + (size_t)v * S;
+        double *arow = p.acc + (size_t)v * S;
 #pragma unroll
-        for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
-        for (int base = 0; base < na; base += 32) {
-            const bool valid = base + lane < na;
-            const int wv = wv_next;
-            wv_next = base + 32 + lane < na ? p.col[a0 + base + 32 + lane] : 0;
-            uint64_t tm[W];
+        for (int k = 0; k < W; ++k) {
+            const unsigned two = (unsigned)((F[k] >> (2 * lane)) & 3ull);
+            if (!two) continue;
+            double2 *sp = reinterpret_cast<double2 *>(srow + 64 * k + 2 * lane);
+            double2 *ap = reinterpret_cast<double2 *>(arow + 64 * k + 2 * lane);
+            const double2 sv = *sp;
+            const double2 av = *ap;
+            double2 cv = sv;
+            double dd[2] = {0.0, 0.0};
+            if (two & 1u) {
+                dd[0] = sv.x * av.x;
+                cv.x = (1.0 + dd[0]) / sv.x;
+            }
+            if (two & 2u) {
+                dd[1] = sv.y * av.y;
+                cv.y = (1.0 + dd[1]) / sv.y;
+            }
+            *sp = cv;
+            *ap = make_double2(0.0, 0.0);
+            if (qm) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!((two >> j) & 1u)) continue;
+                    const int s = 64 * k + 2 * lane + j;
+                    uint64_t x = qm & s_need[s];
+                    while (x) {
+                        const int q = __ffsll((long long)x) - 1;
+                        x &= x - 1;
+                        p.dep[s * 64 + q] = dd[j];
+                    }
+                }
+            }
+        }
+    }
+    if (!next) return;
+    // in-arc chunks of level L for the push into level L - 1
+    const int CH = p.chunk_arcs;
+    unsigned long long *icnt = &p.lev_grab[2 * ((long long)p.maxlev + 2) + L];
+    for (long long b = e0 + gwarp * 32; b < e1; b += nwarps * 32) {
+        const long long e = b + lane;
+        int v = 0, nch = 0;
+        long long rb = 0, re = 0;
+        if (e < e1) {
             bool any = false;
-            if (valid) {
-                const uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    tm[w] = F[w] & wrow[nx * W + w];
-                    any |= tm[w] != 0ull;
-                }
-                st.arcs += 1;
+            for (int k = 0; k < W; ++k) any |= (p.hm[(size_t)e * W + k] & s_act_next[k]) != 0ull;
+            if (any) {
+                v = p.hv[e];
+                rb = p.roff[v];
+                re = p.roff[v + 1];
+                nch = (int)((re - rb + CH - 1) / CH);
+            }
+        }
+        int x = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        const int tot = __shfl_sync(kFull, x, 31);
+        if (tot == 0) continue;
+        unsigned long long cb = 0;
+        if (lane == 0) cb = atomicAdd(icnt, (unsigned long long)tot);
+        cb = __shfl_sync(kFull, cb, 0);
+        if (nch) {
+            const long long c0 = (long long)cb + (x - nch);
+            if (c0 + nch > p.ccap) {
+                set_err(p.ctr, kDevChunkOverflow);
             } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) tm[w] = 0ull;
-            }
-            unsigned bal = __ballot_sync(kFull, any);
-            while (bal) {
-                // issue: tight heads in arc order until the stage is full
-                unsigned done = 0u;
-                int units = 0;
-                unsigned scan = bal;
-                while (scan) {
-                    const int i = __ffs(scan) - 1;
-                    int need = 0;
-                    uint64_t tmi[W];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        tmi[w] = __shfl_sync(kFull, tm[w], i);
-                        need += __popcll((tmi[w] | (tmi[w] >> 1)) & kEven);
-                    }
-                    if (units + need > KU && units > 0) break;
-                    const int wi = __shfl_sync(kFull, wv, i);
-                    const double *crow = p.sigma + (size_t)wi * S;
-                    int off = units;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        const uint64_t pm = (tmi[w] | (tmi[w] >> 1)) & kEven;
-                        if ((pm >> (2 * lane)) & 1ull) {
-                            const int slot = off + __popcll(pm & below);
-                            cp_async16(stage + 2 * slot, crow + 64 * w + 2 * lane, 16);
-                        }
-                        off += __popcll(pm);
-                    }
-                    units = off;
-                    done |= 1u << i;
-                    scan &= scan - 1;
-                }
-                cp_async_wait_all();
-                __syncwarp();
-                // consume the same heads in the same order
-                int offc = 0;
-                unsigned cons = done;
-                while (cons) {
-                    const int i = __ffs(cons) - 1;
-                    cons &= cons - 1;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        const uint64_t tmi = __shfl_sync(kFull, tm[w], i);
-                        const uint64_t pm = (tmi | (tmi >> 1)) & kEven;
-                        const unsigned two = (unsigned)((tmi >> (2 * lane)) & 3ull);
-                        if (two) {
-                            const int slot = offc + __popcll(pm & below);
-                            const double2 val = *reinterpret_cast<const double2 *>(stage + 2 * slot);
-                            if (two & 1u) acc[2 * w] += val.x;
-                            if (two & 2u) acc[2 * w + 1] += val.y;
-                        }
-                        offc += __popcll(pm);
-                    }
-                }
-                __syncwarp();
-                bal &= ~done;
-            }
-        }
-        if (nch == 1) {
-            finalize_entry<W>(p, v, F, acc, s_need, lane);
-        } else {
-            const long long slot0 = p.hslot[e];
-            double *prow = p.partial + (size_t)(slot0 + k) * S;
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                __stcg(reinterpret_cast<double2 *>(prow + 64 * w + 2 * lane), make_double2(acc[2 * w], acc[2 * w + 1]));
-            __threadfence();
-            int prev = 0;
-            if (lane == 0) prev = atomicAdd(&p.pdone[slot0], 1);
-            prev = __shfl_sync(kFull, prev, 0);
-            if (prev == nch - 1) {
-                __threadfence();
-#pragma unroll
-                for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
                 for (int kk = 0; kk < nch; ++kk) {
-                    const double *q = p.partial + (size_t)(slot0 + kk) * S;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        const double2 x = __ldcg(reinterpret_cast<const double2 *>(q + 64 * w + 2 * lane));
-                        acc[2 * w] += x.x;
-                        acc[2 * w + 1] += x.y;
-                    }
+                    const long long a0 = rb + (long long)kk * CH;
+                    store_chunk(&p.chunks[c0 + kk], v, (int)e, kk, nch, a0, (int)(min(re, a0 + CH) - a0));
                 }
-                if (lane == 0) p.pdone[slot0] = 0;
-                finalize_entry<W>(p, v, F, acc, s_need, lane);
             }
         }
+    }
+    // parity slot of levels L + 1 and L - 1: clear level L + 1, set level L - 1
+    const int slot = 1 + ((L + 1) & 1);
+    if (L + 1 <= Lmax) {
+        const long long f0 = p.lev_start[L + 1], f1 = f0 + (long long)p.lev_cnt[L + 1];
+        for (long long e = f0 + gthr; e < f1; e += nthr) {
+            uint64_t *row = p.vs + (size_t)p.hv[e] * stride;
+#pragma unroll
+            for (int k = 0; k < W; ++k)
+                atomicAnd((unsigned long long *)&row[slot * W + k], ~(unsigned long long)p.hm[e * W + k]);
+        }
+    }
+    const long long g0 = p.lev_start[L - 1], g1 = g0 + (long long)p.lev_cnt[L - 1];
+    for (long long e = g0 + gthr; e < g1; e += nthr) {
+        uint64_t *row = p.vs + (size_t)p.hv[e] * stride;
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+            atomicOr((unsigned long long *)&row[slot * W + k], (unsigned long long)p.hm[e * W + k]);
     }
 }
 
 template <int W, int MODE, int MINB>
 __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
     constexpr int S = 64 * W;
-    extern __shared__ __align__(16) double s_stage_all[];
     const int lane = threadIdx.x & 31;
     const long long wpb = blockDim.x >> 5;
     const long long gwarp = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
     const long long nwarps = (long long)gridDim.x * wpb;
     const long long gthr = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
-    double *stage = s_stage_all + (threadIdx.x >> 5) * (kStageBytes / 8);
     uint32_t gen = 0;
     __shared__ uint64_t s_need[S];
     __shared__ int32_t s_minql[S];
     __shared__ uint64_t s_active[W];
+    __shared__ uint64_t s_active_next[W];
     __shared__ int32_t s_lstop;
     Stats st;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -603,33 +606,25 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
             const int lstop = s_lstop;
             for (int Lb = Lmax; Lb >= lstop && lstop <= Lmax; --Lb) {
                 if (threadIdx.x < W) {
-                    uint64_t a = 0;
-                    for (int b = 0; b < 64; ++b)
-                        if (s_minql[threadIdx.x * 64 + b] <= Lb) a |= 1ull << b;
+                    uint64_t a = 0, an = 0;
+                    for (int b = 0; b < 64; ++b) {
+                        const int mq = s_minql[threadIdx.x * 64 + b];
+                        if (mq <= Lb) a |= 1ull << b;
+                        if (mq <= Lb - 1) an |= 1ull << b;
+                    }
                     s_active[threadIdx.x] = a;
+                    s_active_next[threadIdx.x] = an;
                 }
                 __syncthreads();
-                const int cur = 1 + (Lb & 1);
-                if (Lb + 2 <= Lmax) {
-                    const long long e0 = p.lev_start[Lb + 2], e1 = e0 + (long long)p.lev_cnt[Lb + 2];
-                    for (long long e = e0 + gthr; e < e1; e += nthr) {
-                        uint64_t *row = p.vs + (size_t)p.hv[e] * p.vs_stride;
-#pragma unroll
-                        for (int w = 0; w < W; ++w)
-                            atomicAnd((unsigned long long *)&row[cur * W + w], ~(unsigned long long)p.hm[e * W + w]);
+                if (Lb < Lmax) {
+                    const long long ic = (long long)ld_vol(&p.lev_grab[2 * ((long long)p.maxlev + 2) + Lb + 1]);
+                    if (ic > 0) {
+                        push_level<W>(p, Lb, ic, s_active, nwarps, st);
+                        if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
                     }
                 }
-                {
-                    const long long e0 = p.lev_start[Lb], e1 = e0 + (long long)p.lev_cnt[Lb];
-                    for (long long e = e0 + gthr; e < e1; e += nthr) {
-                        uint64_t *row = p.vs + (size_t)p.hv[e] * p.vs_stride;
-#pragma unroll
-                        for (int w = 0; w < W; ++w)
-                            atomicOr((unsigned long long *)&row[cur * W + w], (unsigned long long)p.hm[e * W + w]);
-                    }
-                }
-                backward_level<W>(p, Lb, p.lev_cstart[Lb], (long long)p.lev_ccnt[Lb], s_active, s_need, gwarp, nwarps,
-                                  stage, st);
+                settle_level<W>(p, Lb, Lmax, Lb - 1 >= lstop, s_active, s_active_next, s_need, gwarp, nwarps, gthr,
+                                nthr);
                 if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
         }
@@ -690,6 +685,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                     p.lev_ccnt[l] = 0ull;
                     p.lev_grab[l] = 0ull;
                     p.lev_grab[p.maxlev + 2 + l] = 0ull;
+                    p.lev_grab[2 * (p.maxlev + 2) + l] = 0ull;
                 }
                 if (threadIdx.x == 0) p.ctr->pslots = 0ull;
             }
@@ -713,8 +709,7 @@ template <int W, int MODE, int MINB>
 bc_status launch(bc_graph *g, TravParams &p) {
     auto kern = trav_kernel<W, MODE, MINB>;
     const int threads = g->block_threads;
-    const size_t smem = (size_t)(threads / 32) * kStageBytes;
-    BCD_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = 0;
     int per_sm = 0;
     BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return set_error(BC_E_INTERNAL, "traversal kernel cannot be resident");
@@ -736,7 +731,8 @@ bc_status reset_dense_state(bc_graph *g) {
     BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * (size_t)(ws.maxlev + 2), g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_grab, 0, sizeof(unsigned long long) * 6 * (size_t)(ws.maxlev + 2), g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)ws.pcap, g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)(g->weighted ? ws.pcap : 1), g->stream));
+    BCD_CUDA(cudaMemsetAsync(ws.acc, 0, sizeof(double) * (g->weighted ? (size_t)1 : (size_t)ws.n * 64 * ws.W), g->stream));
     if (ws.dist) {
         BCD_CUDA(cudaMemsetAsync(ws.dist, 0xff, sizeof(uint64_t) * (size_t)ws.n * 64 * ws.W, g->stream));
         BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * 2 * (size_t)ws.ring, g->stream));
@@ -751,6 +747,9 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.vs_stride = ws.vs_stride;
         p.tag = ws.tag;
         p.sigma = ws.sigma;
+        p.acc = ws.acc;
+        p.roff = g->d_roff;  // R(G): in-arcs for the backward push and the weighted sigma pull
+        p.rcol = g->d_rcol;
         p.hv = ws.hv;
         p.hm = ws.hm;
         p.hslot = ws.hslot;
