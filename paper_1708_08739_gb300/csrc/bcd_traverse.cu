@@ -248,27 +248,20 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
 #pragma unroll
                 for (int w = 0; w < W; ++w) nm[w] = 0ull;
             }
-            bool app = false;
-            int wnch = 0;
+            // heads with new sources: mark them for the next level and claim
+            // the level's entry; the claim's answer (and the row bounds) are
+            // used only after the sigma adds, so their round trips overlap
+            int old = 0x7fffffff;
             long long wrb = 0, wre = 0;
             if (any) {
                 uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
                 for (int w = 0; w < W; ++w)
                     if (nm[w]) atomicOr((unsigned long long *)&wrow[nxt * W + w], (unsigned long long)nm[w]);
-                const int old = atomicMax(&p.tag[wv], L + 1);
-                app = old < L + 1;
-                if (app) {
-                    wrb = p.off[wv];
-                    wre = p.off[wv + 1];
-                    wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
-                    if (MODE == kModeSpd && old < 0) {
-                        st.vb += 1;
-                        st.eb += (unsigned)(wre - wrb);
-                    }
-                }
+                old = atomicMax(&p.tag[wv], L + 1);
+                wrb = p.off[wv];
+                wre = p.off[wv + 1];
             }
-            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
             if (MODE == kModeSpd) {
                 // two tight heads per step: their shuffles and atomics overlap
                 unsigned bal = __ballot_sync(kFull, any);
@@ -300,6 +293,16 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     }
                 }
             }
+            const bool app = any && old < L + 1;
+            int wnch = 0;
+            if (app) {
+                wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
+                if (MODE == kModeSpd && old < 0) {
+                    st.vb += 1;
+                    st.eb += (unsigned)(wre - wrb);
+                }
+            }
+            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
         }
     }
 }
