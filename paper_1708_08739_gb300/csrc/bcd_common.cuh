@@ -90,6 +90,7 @@ struct TravParams {
     int64_t *hslot;     // [hcap]
     int64_t hcap;
     Chunk *chunks;      // [ccap]
+    Chunk *ichunks;     // [ccap] in-arc (R(G)) chunks of the entries, per level (unweighted SPD)
     int64_t ccap;
     double *partial;    // [pcap * S]
     int32_t *pdone;     // [pcap]
@@ -99,6 +100,7 @@ struct TravParams {
     unsigned long long *lev_grab;  // [2 * (maxlev + 2)] chunk hand-out counters, forward then backward
     int64_t *lev_start;            // [maxlev + 2]
     int64_t *lev_cstart;           // [maxlev + 2]
+    int64_t *lev_icstart;          // [maxlev + 2] first in-arc chunk of each level
     int32_t maxlev;
     int32_t pad1;
     // tiles
@@ -157,6 +159,7 @@ struct bcd_workspace {
     int64_t *hslot = nullptr;
     int64_t hcap = 0;
     bcd::Chunk *chunks = nullptr;
+    bcd::Chunk *ichunks = nullptr;
     int64_t ccap = 0;
     double *partial = nullptr;
     int32_t *pdone = nullptr;
@@ -166,6 +169,7 @@ struct bcd_workspace {
     unsigned long long *lev_grab = nullptr;
     int64_t *lev_start = nullptr;
     int64_t *lev_cstart = nullptr;
+    int64_t *lev_icstart = nullptr;
     int32_t maxlev = 0;
     // per-group state
     uint64_t *rvmask = nullptr;   // [n]

@@ -176,6 +176,7 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     dev_free(ws.hs);
     dev_free(ws.hslot);
     dev_free(ws.chunks);
+    dev_free(ws.ichunks);
     dev_free(ws.partial);
     dev_free(ws.pdone);
     if (hcap >= (int64_t)INT32_MAX) hcap = (int64_t)INT32_MAX - 1;
@@ -191,6 +192,7 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     BCD_TRY(dev_alloc(&ws.hs, wg ? (size_t)hcap : (size_t)1));
     BCD_TRY(dev_alloc(&ws.hslot, (size_t)1));
     BCD_TRY(dev_alloc(&ws.chunks, (size_t)ccap));
+    BCD_TRY(dev_alloc(&ws.ichunks, wg ? (size_t)1 : (size_t)ccap));
     BCD_TRY(dev_alloc(&ws.partial, wg ? (size_t)pcap : (size_t)1));
     BCD_TRY(dev_alloc(&ws.pdone, wg ? (size_t)pcap : (size_t)1));
     BCD_CUDA(cudaMemsetAsync(ws.pdone, 0, sizeof(int32_t) * (size_t)(wg ? pcap : 1), g->stream));
@@ -206,6 +208,7 @@ bc_status alloc_levels(bc_graph *g, int64_t maxlev) {
     dev_free(ws.lev_grab);
     dev_free(ws.lev_start);
     dev_free(ws.lev_cstart);
+    dev_free(ws.lev_icstart);
     dev_free(ws.lev_dist);
     ws.maxlev = (int32_t)maxlev;
     const size_t L = (size_t)maxlev + 2;
@@ -214,6 +217,7 @@ bc_status alloc_levels(bc_graph *g, int64_t maxlev) {
     BCD_TRY(dev_alloc(&ws.lev_grab, 6 * L));
     BCD_TRY(dev_alloc(&ws.lev_start, L));
     BCD_TRY(dev_alloc(&ws.lev_cstart, L));
+    BCD_TRY(dev_alloc(&ws.lev_icstart, L));
     if (g->weighted) BCD_TRY(dev_alloc(&ws.lev_dist, L));
     BCD_CUDA(cudaMemsetAsync(ws.lev_cnt, 0, sizeof(unsigned long long) * L, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.lev_ccnt, 0, sizeof(unsigned long long) * L, g->stream));
@@ -287,6 +291,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.hs);
     dev_free(ws.hslot);
     dev_free(ws.chunks);
+    dev_free(ws.ichunks);
     dev_free(ws.partial);
     dev_free(ws.pdone);
     dev_free(ws.lev_cnt);
@@ -294,6 +299,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.lev_grab);
     dev_free(ws.lev_start);
     dev_free(ws.lev_cstart);
+    dev_free(ws.lev_icstart);
     dev_free(ws.rvmask);
     dev_free(ws.need);
     dev_free(ws.qmask);

@@ -36,39 +36,58 @@ namespace {
 
 using namespace dev;
 
-// Appends the vertices a warp discovered at level L+1 (one entry and nch
-// chunks each), with one pair of counter atomics per warp.
+// Appends the vertices a warp discovered at level L+1: one entry and its
+// out-arc chunks each and, in SPD mode, the in-arc (R(G)) chunks the backward
+// pass pushes along, with one set of counter atomics per warp.
 template <int W, int MODE>
 __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app, int wv, int wnch, long long wrb,
-                                            long long wre, long long es1, long long cs1, int lane) {
+                                            long long wre, int winch, long long wirb, long long wire, long long es1,
+                                            long long cs1, long long ics1, int lane) {
     const unsigned am = __ballot_sync(kFull, app);
     if (am == 0) return;
     const int rank = __popc(am & ((1u << lane) - 1u));
     const int ne = __popc(am);
     int x = app ? wnch : 0;
+    int xi = app ? winch : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+        const int yi = __shfl_up_sync(kFull, xi, o);
+        if (lane >= o) {
+            x += y;
+            xi += yi;
+        }
     }
     const int tot = __shfl_sync(kFull, x, 31);
-    unsigned long long eb = 0, cb = 0;
+    const int toti = __shfl_sync(kFull, xi, 31);
+    unsigned long long eb = 0, cb = 0, ib = 0;
     if (lane == 0) {
         eb = atomicAdd(&p.lev_cnt[L + 1], (unsigned long long)ne);
         cb = atomicAdd(&p.lev_ccnt[L + 1], (unsigned long long)tot);
+        if (MODE == kModeSpd && toti)
+            ib = atomicAdd(&p.lev_grab[2 * ((long long)p.maxlev + 2) + L + 1], (unsigned long long)toti);
     }
     eb = __shfl_sync(kFull, eb, 0);
     cb = __shfl_sync(kFull, cb, 0);
+    if (MODE == kModeSpd) ib = __shfl_sync(kFull, ib, 0);
     if (app) {
         const long long e = es1 + (long long)eb + rank;
         const long long c0 = cs1 + (long long)cb + (x - wnch);
+        const long long i0 = ics1 + (long long)ib + (xi - winch);
         if (e >= p.hcap) {
             set_err(p.ctr, kDevHistOverflow);
-        } else if (c0 + wnch > p.ccap) {
+        } else if (c0 + wnch > p.ccap || (MODE == kModeSpd && i0 + winch > p.ccap)) {
             set_err(p.ctr, kDevChunkOverflow);
         } else {
             p.hv[e] = wv;
             emit_chunks(p, c0, wv, (int)e, wnch, wrb, wre);
+            if (MODE == kModeSpd) {
+                const int CH = p.chunk_arcs;
+                for (int k = 0; k < winch; ++k) {
+                    const long long a0 = wirb + (long long)k * CH;
+                    store_chunk(&p.ichunks[i0 + k], wv, (int)e, k, winch, a0, (int)(min(wire, a0 + CH) - a0));
+                }
+            }
         }
     }
 }
@@ -160,7 +179,7 @@ __device__ __forceinline__ void flush_stats(Counters *c, Stats &st, int lane) {
 
 template <int W, int MODE>
 __device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
-                              long long cs1, Stats &st, const uint64_t *s_need,
+                              long long cs1, long long ics1, Stats &st, const uint64_t *s_need,
                               long long gwarp, long long nwarps) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
@@ -252,7 +271,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
             // the level's entry; the claim's answer (and the row bounds) are
             // used only after the sigma adds, so their round trips overlap
             int old = 0x7fffffff;
-            long long wrb = 0, wre = 0;
+            long long wrb = 0, wre = 0, wirb = 0, wire = 0;
             if (any) {
                 uint64_t *wrow = p.vs + (size_t)wv * stride;
 #pragma unroll
@@ -261,6 +280,10 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                 old = atomicMax(&p.tag[wv], L + 1);
                 wrb = p.off[wv];
                 wre = p.off[wv + 1];
+                if (MODE == kModeSpd) {
+                    wirb = p.roff[wv];
+                    wire = p.roff[wv + 1];
+                }
             }
             if (MODE == kModeSpd) {
                 // two tight heads per step: their shuffles and atomics overlap
@@ -294,37 +317,40 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                 }
             }
             const bool app = any && old < L + 1;
-            int wnch = 0;
+            int wnch = 0, winch = 0;
             if (app) {
                 wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
+                if (MODE == kModeSpd) winch = (int)((wire - wirb + CH - 1) / CH);
                 if (MODE == kModeSpd && old < 0) {
                     st.vb += 1;
                     st.eb += (unsigned)(wre - wrb);
                 }
             }
-            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, es1, cs1, lane);
+            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, winch, wirb, wire, es1, cs1, ics1, lane);
         }
     }
 }
 
-// Eq. 4, push form, for level L: the entries of level L + 1 send
-// c_s(w) = (1 + delta_s(w)) / sigma_s(w) back along their in-arcs (v, w) that
-// are tight for an active source s (v at level L for s), adding it to the
-// accumulator acc_s(v) with fp64 atomic adds. The in-arc chunks of level
-// L + 1 were cut in the previous step. Lane l holds sources l + 32 i, as in
-// the forward pass; two tight tails are handled per step.
+// Eq. 4, push form, from level L into level L - 1: each entry w of level L
+// sends c_s(w) = (1 + delta_s(w)) / sigma_s(w), with delta_s(w) =
+// sigma_s(w) * acc_s(w) complete (level L + 1 pushed into it in the previous
+// step), back along its in-arcs (v, w) that are tight for a source s still
+// active at L - 1 (v at level L - 1 for s), adding it to acc_s(v) with fp64
+// atomic adds. c is formed on the fly from the sigma and acc slabs, which this
+// step only reads for level-L pairs. The in-arc chunks of level L were cut in
+// the forward pass. Lane l holds sources l + 32 i; two tight tails per step.
 template <int W>
-__device__ void push_level(const TravParams &p, int L, long long ccnt, const uint64_t *s_act, long long nwarps,
-                           Stats &st) {
+__device__ void push_level(const TravParams &p, int L, long long ics, long long ccnt, const uint64_t *s_act,
+                           long long nwarps, Stats &st) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
     const int lane = threadIdx.x & 31;
-    const int cur = 1 + (L & 1);  // parity slot holding the level-L masks
+    const int par = 1 + ((L - 1) & 1);  // parity slot holding the level-(L-1) masks
     const int stride = p.vs_stride;
     ChunkGrabber grab(&p.lev_grab[p.maxlev + 2 + L], ccnt, nwarps);
     long long c;
     while (grab.next(c, lane)) {
-        const Chunk ch = load_chunk(&p.chunks[c]);
+        const Chunk ch = load_chunk(&p.ichunks[ics + c]);
         const int w = ch.v;
         const long long a0 = ch.a0;
         const int na = ch.na;
@@ -332,9 +358,15 @@ __device__ void push_level(const TravParams &p, int L, long long ccnt, const uin
         uint64_t F[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) F[k] = p.hm[(size_t)ch.e * W + k] & s_act[k];
-        double cw[PL];
+        double sw[PL], aw[PL], cw[PL];
 #pragma unroll
-        for (int ii = 0; ii < PL; ++ii) cw[ii] = p.sigma[(size_t)w * S + lane + 32 * ii];
+        for (int ii = 0; ii < PL; ++ii) {
+            sw[ii] = p.sigma[(size_t)w * S + lane + 32 * ii];
+            aw[ii] = p.acc[(size_t)w * S + lane + 32 * ii];
+        }
+#pragma unroll
+        for (int ii = 0; ii < PL; ++ii)
+            cw[ii] = mask_bit<W>(F, lane + 32 * ii) ? (1.0 + sw[ii] * aw[ii]) / sw[ii] : 0.0;
         for (int base = 0; base < na; base += 32) {
             const bool valid = base + lane < na;
             const int v = vnext;
@@ -345,7 +377,7 @@ __device__ void push_level(const TravParams &p, int L, long long ccnt, const uin
                 const uint64_t *row = p.vs + (size_t)v * stride;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    tm[k] = F[k] & row[cur * W + k];
+                    tm[k] = F[k] & row[par * W + k];
                     any |= tm[k] != 0ull;
                 }
                 st.arcs += 1;
@@ -381,121 +413,49 @@ __device__ void push_level(const TravParams &p, int L, long long ccnt, const uin
     }
 }
 
-// Second phase of a backward step: delta and c for the entries of level L
-// (their accumulators are complete), then, when the pass goes on to level
-// L - 1, the in-arc chunks of level L (entries with a source active at
-// L - 1) and the parity masks of level L - 1 (in the slot that held level
-// L + 1). Lane l holds the source pairs (64 k + 2 l, 64 k + 2 l + 1).
+// The rest of a backward step at level L, one thread per entry: delta_s(r_q)
+// for the query vertices among the level-L entries (their accumulators are
+// complete), and, when the pass goes on, the parity slot shared by levels L
+// and L - 2: the level-L bits leave it and the level-(L - 2) bits enter it
+// (the push from L - 1 reads them in the next step).
 template <int W>
-__device__ void settle_level(const TravParams &p, int L, int Lmax, bool next, const uint64_t *s_act,
-                             const uint64_t *s_act_next, const uint64_t *s_need, long long gwarp, long long nwarps,
-                             long long gthr, long long nthr) {
+__device__ void level_outputs(const TravParams &p, int L, bool swap, bool set_next, const uint64_t *s_act,
+                              const uint64_t *s_need, long long gthr, long long nthr) {
     constexpr int S = 64 * W;
-    const int lane = threadIdx.x & 31;
     const int stride = p.vs_stride;
+    const int slot = 1 + (L & 1);
     const long long e0 = p.lev_start[L], e1 = e0 + (long long)p.lev_cnt[L];
-    for (long long e = e0 + gwarp; e < e1; e += nwarps) {
-        uint64_t F[W];
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            F[k] = p.hm[(size_t)e * W + k] & s_act[k];
-            any |= F[k] != 0ull;
-        }
-        if (!any) continue;
+    for (long long e = e0 + gthr; e < e1; e += nthr) {
         const int v = p.hv[e];
+        uint64_t F[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) F[k] = p.hm[(size_t)e * W + k];
+        if (swap) {
+            uint64_t *row = p.vs + (size_t)v * stride;
+#pragma unroll
+            for (int k = 0; k < W; ++k) atomicAnd((unsigned long long *)&row[slot * W + k], ~(unsigned long long)F[k]);
+        }
         const uint64_t qm = p.qmask[v];
-        double *srow = p.sigma + (size_t)v * S;
-        double *arow = p.acc + (size_t)v * S;
+        if (!qm) continue;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const unsigned two = (unsigned)((F[k] >> (2 * lane)) & 3ull);
-            if (!two) continue;
-            double2 *sp = reinterpret_cast<double2 *>(srow + 64 * k + 2 * lane);
-            double2 *ap = reinterpret_cast<double2 *>(arow + 64 * k + 2 * lane);
-            const double2 sv = *sp;
-            const double2 av = *ap;
-            double2 cv = sv;
-            double dd[2] = {0.0, 0.0};
-            if (two & 1u) {
-                dd[0] = sv.x * av.x;
-                cv.x = (1.0 + dd[0]) / sv.x;
-            }
-            if (two & 2u) {
-                dd[1] = sv.y * av.y;
-                cv.y = (1.0 + dd[1]) / sv.y;
-            }
-            *sp = cv;
-            *ap = make_double2(0.0, 0.0);
-            if (qm) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    if (!((two >> j) & 1u)) continue;
-                    const int s = 64 * k + 2 * lane + j;
-                    uint64_t x = qm & s_need[s];
-                    while (x) {
-                        const int q = __ffsll((long long)x) - 1;
-                        x &= x - 1;
-                        p.dep[s * 64 + q] = dd[j];
-                    }
+            uint64_t b = F[k] & s_act[k];
+            while (b) {
+                const int s = 64 * k + __ffsll((long long)b) - 1;
+                b &= b - 1;
+                uint64_t x = qm & s_need[s];
+                if (!x) continue;
+                const double d = p.sigma[(size_t)v * S + s] * p.acc[(size_t)v * S + s];
+                while (x) {
+                    const int q = __ffsll((long long)x) - 1;
+                    x &= x - 1;
+                    p.dep[s * 64 + q] = d;
                 }
             }
         }
     }
-    if (!next) return;
-    // in-arc chunks of level L for the push into level L - 1
-    const int CH = p.chunk_arcs;
-    unsigned long long *icnt = &p.lev_grab[2 * ((long long)p.maxlev + 2) + L];
-    for (long long b = e0 + gwarp * 32; b < e1; b += nwarps * 32) {
-        const long long e = b + lane;
-        int v = 0, nch = 0;
-        long long rb = 0, re = 0;
-        if (e < e1) {
-            bool any = false;
-#pragma unroll
-            for (int k = 0; k < W; ++k) any |= (p.hm[(size_t)e * W + k] & s_act_next[k]) != 0ull;
-            if (any) {
-                v = p.hv[e];
-                rb = p.roff[v];
-                re = p.roff[v + 1];
-                nch = (int)((re - rb + CH - 1) / CH);
-            }
-        }
-        int x = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        const int tot = __shfl_sync(kFull, x, 31);
-        if (tot == 0) continue;
-        unsigned long long cb = 0;
-        if (lane == 0) cb = atomicAdd(icnt, (unsigned long long)tot);
-        cb = __shfl_sync(kFull, cb, 0);
-        if (nch) {
-            const long long c0 = (long long)cb + (x - nch);
-            if (c0 + nch > p.ccap) {
-                set_err(p.ctr, kDevChunkOverflow);
-            } else {
-                for (int kk = 0; kk < nch; ++kk) {
-                    const long long a0 = rb + (long long)kk * CH;
-                    store_chunk(&p.chunks[c0 + kk], v, (int)e, kk, nch, a0, (int)(min(re, a0 + CH) - a0));
-                }
-            }
-        }
-    }
-    // parity slot of levels L + 1 and L - 1: clear level L + 1, set level L - 1
-    const int slot = 1 + ((L + 1) & 1);
-    if (L + 1 <= Lmax) {
-        const long long f0 = p.lev_start[L + 1], f1 = f0 + (long long)p.lev_cnt[L + 1];
-        for (long long e = f0 + gthr; e < f1; e += nthr) {
-            uint64_t *row = p.vs + (size_t)p.hv[e] * stride;
-#pragma unroll
-            for (int k = 0; k < W; ++k)
-                atomicAnd((unsigned long long *)&row[slot * W + k], ~(unsigned long long)p.hm[e * W + k]);
-        }
-    }
-    const long long g0 = p.lev_start[L - 1], g1 = g0 + (long long)p.lev_cnt[L - 1];
+    if (!set_next) return;
+    const long long g0 = p.lev_start[L - 2], g1 = g0 + (long long)p.lev_cnt[L - 2];
     for (long long e = g0 + gthr; e < g1; e += nthr) {
         uint64_t *row = p.vs + (size_t)p.hv[e] * stride;
 #pragma unroll
@@ -539,18 +499,21 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         }
 
         // ---------------- forward ----------------
-        long long es = 0, cs = 0, es_prev = 0;
+        long long es = 0, cs = 0, ics = 0, es_prev = 0;
         int L = 0;
         long long total = 0;
         for (;;) {
             const long long ecnt = (long long)ld_vol(&p.lev_cnt[L]);
             const long long ccnt = (long long)ld_vol(&p.lev_ccnt[L]);
-            const long long es1 = es + ecnt, cs1 = cs + ccnt;
+            const long long iccnt = (long long)ld_vol(&p.lev_grab[2 * ((long long)p.maxlev + 2) + L]);
+            const long long es1 = es + ecnt, cs1 = cs + ccnt, ics1 = ics + iccnt;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 p.lev_start[L] = es;
                 p.lev_cstart[L] = cs;
                 p.lev_start[L + 1] = es1;
                 p.lev_cstart[L + 1] = cs1;
+                p.lev_icstart[L] = ics;
+                p.lev_icstart[L + 1] = ics1;
             }
             if (L >= 1) {
                 const int nxt = 1 + ((L + 1) & 1);
@@ -562,7 +525,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                         atomicAnd((unsigned long long *)&row[nxt * W + w], ~(unsigned long long)p.hm[e * W + w]);
                 }
             }
-            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, st, s_need, gwarp, nwarps);
+            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, ics1, st, s_need, gwarp, nwarps);
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             total = es1;
             if (ld_vol(&p.lev_cnt[L + 1]) == 0ull) break;
@@ -573,6 +536,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
             es_prev = es;
             es = es1;
             cs = cs1;
+            ics = ics1;
             ++L;
         }
         const int Lmax = L;
@@ -607,28 +571,40 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
             }
             __syncthreads();
             const int lstop = s_lstop;
-            for (int Lb = Lmax; Lb >= lstop && lstop <= Lmax; --Lb) {
-                if (threadIdx.x < W) {
-                    uint64_t a = 0, an = 0;
-                    for (int b = 0; b < 64; ++b) {
-                        const int mq = s_minql[threadIdx.x * 64 + b];
-                        if (mq <= Lb) a |= 1ull << b;
-                        if (mq <= Lb - 1) an |= 1ull << b;
+            if (lstop <= Lmax) {
+                // the parity slot of level Lmax - 1 is empty after the forward pass
+                if (Lmax - 1 >= lstop) {
+                    const int slot = 1 + ((Lmax - 1) & 1);
+                    const long long g0 = p.lev_start[Lmax - 1], g1 = g0 + (long long)p.lev_cnt[Lmax - 1];
+                    for (long long e = g0 + gthr; e < g1; e += nthr) {
+                        uint64_t *row = p.vs + (size_t)p.hv[e] * p.vs_stride;
+#pragma unroll
+                        for (int w = 0; w < W; ++w)
+                            atomicOr((unsigned long long *)&row[slot * W + w], (unsigned long long)p.hm[e * W + w]);
                     }
-                    s_active[threadIdx.x] = a;
-                    s_active_next[threadIdx.x] = an;
+                    if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
                 }
-                __syncthreads();
-                if (Lb < Lmax) {
-                    const long long ic = (long long)ld_vol(&p.lev_grab[2 * ((long long)p.maxlev + 2) + Lb + 1]);
-                    if (ic > 0) {
-                        push_level<W>(p, Lb, ic, s_active, nwarps, st);
-                        if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+                for (int Lb = Lmax; Lb >= lstop; --Lb) {
+                    if (threadIdx.x < W) {
+                        uint64_t a = 0, an = 0;
+                        for (int b = 0; b < 64; ++b) {
+                            const int mq = s_minql[threadIdx.x * 64 + b];
+                            if (mq <= Lb) a |= 1ull << b;
+                            if (mq <= Lb - 1) an |= 1ull << b;
+                        }
+                        s_active[threadIdx.x] = a;
+                        s_active_next[threadIdx.x] = an;
                     }
+                    __syncthreads();
+                    const bool more = Lb > lstop;
+                    level_outputs<W>(p, Lb, more, more && Lb - 2 >= lstop, s_active, s_need, gthr, nthr);
+                    if (more) {
+                        const long long ics = p.lev_icstart[Lb];
+                        const long long ic = (long long)ld_vol(&p.lev_grab[2 * ((long long)p.maxlev + 2) + Lb]);
+                        push_level<W>(p, Lb, ics, ic, s_active_next, nwarps, st);
+                    }
+                    if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
                 }
-                settle_level<W>(p, Lb, Lmax, Lb - 1 >= lstop, s_active, s_active_next, s_need, gwarp, nwarps, gthr,
-                                nthr);
-                if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             }
         }
         if (timer) {
@@ -673,10 +649,14 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
 #pragma unroll
                     for (int w = 0; w < W; ++w) F[w] = p.hm[e * W + w];
                     double *row = p.sigma + (size_t)v * S;
+                    double *arow = p.acc + (size_t)v * S;
 #pragma unroll
                     for (int ii = 0; ii < 2 * W; ++ii) {
                         const int s = lane + 32 * ii;
-                        if (mask_bit<W>(F, s)) row[s] = 0.0;
+                        if (mask_bit<W>(F, s)) {
+                            row[s] = 0.0;
+                            arow[s] = 0.0;
+                        }
                     }
                 }
                 if (lane < p.vs_stride) p.vs[(size_t)v * p.vs_stride + lane] = 0ull;
@@ -758,6 +738,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.hslot = ws.hslot;
         p.hcap = p.mode == kModeReach ? ws.hmcap : ws.hcap;
         p.chunks = ws.chunks;
+        p.ichunks = ws.ichunks;
         p.ccap = ws.ccap;
         p.partial = ws.partial;
         p.pdone = ws.pdone;
@@ -767,6 +748,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.lev_grab = ws.lev_grab;
         p.lev_start = ws.lev_start;
         p.lev_cstart = ws.lev_cstart;
+        p.lev_icstart = ws.lev_icstart;
         p.maxlev = ws.maxlev;
         p.ctr = ws.ctr;
         p.n = g->n;
