@@ -291,9 +291,10 @@ void bc_server_destroy(bc_server *srv);
  *   block_threads  threads per block of the persistent kernel (128..512,
  *                  a multiple of 32);
  *   source_order   how the union of sources is cut into tiles: 1 (default)
- *                  groups sources by their hop distance to the vertex of
- *                  largest in-degree x out-degree, so that a tile's BFS
- *                  levels line up; 2 keeps ascending vertex ids;
+ *                  sorts sources by their hop distance to the vertex of
+ *                  largest in-degree x out-degree, then by out-degree
+ *                  (largest first), so that a tile's BFS levels line up;
+ *                  2 keeps ascending vertex ids;
  *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2
  *                  trades register spills for occupancy);
  *   weighted_words sources per tile of the weighted kernel, in words of 64

@@ -300,7 +300,8 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
                     uint32_t *qflags, unsigned long long *edges);
 bc_status check_graph(bc_graph *g, const char *fn);
 bc_status prepare_ordering(bc_graph *g);
-int32_t hub_level(bc_graph *g, int32_t v);
+// Tile order of a source: hop distance to the hub, then out-degree descending.
+int64_t source_order_key(const bc_graph *g, int32_t v);
 bc_status ensure_weighted_state(bc_graph *g);
 bc_status reset_dense_state(bc_graph *g);
 

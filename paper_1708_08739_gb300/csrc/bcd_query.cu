@@ -494,11 +494,12 @@ bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::
     return BC_OK;
 }
 
-// Tile ordering key: hop distance from each vertex to the hub, the vertex of
-// largest in-degree x out-degree (one reach traversal of R(G) from the hub,
-// cached per graph). Sources at equal distance to the hub have closely
-// aligned BFS level profiles, so a tile of them touches each vertex at fewer
-// distinct levels.
+// Tile ordering key, first part: hop distance from each vertex to the hub,
+// the vertex of largest in-degree x out-degree (one reach traversal of R(G)
+// from the hub, cached per graph). Sources at equal distance to the hub have
+// closely aligned BFS level profiles, so a tile of them touches each vertex at
+// fewer distinct levels; among them, sources of similar out-degree reach the
+// bulk of the graph at the same level (see source_order_key).
 static bc_status ensure_hub_levels(bc_graph *g) {
     std::vector<int32_t> &h_lev = g->h_hublev;
     bcd_workspace &ws = g->ws;
@@ -535,22 +536,18 @@ static bc_status ensure_hub_levels(bc_graph *g) {
     return BC_OK;
 }
 
-// Stable reorder of the source union by hub distance (unreached last).
+// Reorder of the source union by source_order_key (ties keep ascending ids).
 static bc_status order_sources(bc_graph *g, int64_t nd) {
     bcd_workspace &ws = g->ws;
     BCD_TRY(ensure_hub_levels(g));
-    const std::vector<int32_t> &h_lev = g->h_hublev;
     cudaStream_t s = g->stream;
     std::vector<int32_t> d((size_t)nd), out((size_t)nd);
     BCD_CUDA(cudaMemcpyAsync(d.data(), ws.dlist, sizeof(int32_t) * (size_t)nd, cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaStreamSynchronize(s));
-    int32_t maxk = 0;
-    for (int64_t i = 0; i < nd; ++i) maxk = std::max(maxk, h_lev[d[i]]);
-    std::vector<int64_t> cnt((size_t)maxk + 3, 0);
-    auto key = [&](int32_t v) { return h_lev[v] < 0 ? maxk + 1 : h_lev[v]; };
-    for (int64_t i = 0; i < nd; ++i) cnt[key(d[i]) + 1]++;
-    for (size_t k = 1; k < cnt.size(); ++k) cnt[k] += cnt[k - 1];
-    for (int64_t i = 0; i < nd; ++i) out[cnt[key(d[i])]++] = d[i];
+    std::vector<std::pair<int64_t, int32_t>> kv((size_t)nd);
+    for (int64_t i = 0; i < nd; ++i) kv[i] = {source_order_key(g, d[i]), d[i]};
+    std::sort(kv.begin(), kv.end());
+    for (int64_t i = 0; i < nd; ++i) out[i] = kv[i].second;
     BCD_CUDA(cudaMemcpyAsync(ws.dlist, out.data(), sizeof(int32_t) * (size_t)nd, cudaMemcpyHostToDevice, s));
     positions<<<grid_for(g, nd, 256), 256, 0, s>>>(ws.dlist, nd, ws.posd);
     g->launches += 1;
@@ -893,10 +890,12 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
     return BC_OK;
 }
 
-int32_t hub_level(bc_graph *g, int32_t v) {
-    if ((int64_t)g->h_hublev.size() != g->n) return 0;
-    const int32_t l = g->h_hublev[v];
-    return l < 0 ? 0x7fffffff : l;
+int64_t source_order_key(const bc_graph *g, int32_t v) {
+    if (g->source_order != 1) return v;
+    int64_t lev = 0;
+    if ((int64_t)g->h_hublev.size() == g->n) lev = g->h_hublev[v] < 0 ? 0x7fffffff : g->h_hublev[v];
+    const int64_t deg = std::min<int64_t>(g->h_off[v + 1] - g->h_off[v], 0x7fffffff);
+    return (lev << 31) | (0x7fffffff - deg);
 }
 
 bc_status prepare_ordering(bc_graph *g) { return g->source_order == 1 ? ensure_hub_levels(g) : BC_OK; }

@@ -199,11 +199,12 @@ bool bc_server::run_slice_once() {
             if (slots[s] && slots[s]->outstanding <= 0) complete(slots[s], BC_OK);
         return false;
     }
-    // tiles of sources at similar hop distance to the hub (aligned levels)
+    // tiles of sources at similar hop distance to the hub and of similar
+    // out-degree (aligned levels)
     std::vector<size_t> order(take.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
-        return bcd::hub_level(g, take[a]) < bcd::hub_level(g, take[b]);
+        return bcd::source_order_key(g, take[a]) < bcd::source_order_key(g, take[b]);
     });
     const int64_t ntiles = ((int64_t)take.size() + S - 1) / S;
     std::vector<int32_t> srcs((size_t)ntiles * S, -1);
