@@ -40,7 +40,7 @@ WORKLOAD = "rmat20_ef16_exact64"
 # profiles/trav_kernel_rmat20_sampled512_w2.md (R-MAT scale 20, 128-source
 # tiles); a workload without an entry, or a kernel changed since the capture,
 # reports traffic null
-TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 9.73}
+TRAFFIC_BYTES_PER_EDGE = {}
 
 
 def log(*a):

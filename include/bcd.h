@@ -292,8 +292,9 @@ void bc_server_destroy(bc_server *srv);
  *                  a multiple of 32);
  *   source_order   how the union of sources is cut into tiles: 1 (default)
  *                  sorts sources by their hop distance to the vertex of
- *                  largest in-degree x out-degree, then by out-degree
- *                  (largest first), so that a tile's BFS levels line up;
+ *                  largest in-degree x out-degree, then by the number of
+ *                  arcs two hops away (largest first), so that a tile's BFS
+ *                  levels line up;
  *                  2 keeps ascending vertex ids;
  *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2
  *                  trades register spills for occupancy);

@@ -234,7 +234,8 @@ struct bc_graph {
     uint32_t *d_rw = nullptr;
     std::vector<int64_t> h_off;   // forward offsets (degree checks)
     std::vector<int64_t> h_roff;  // reverse offsets
-    std::vector<int32_t> h_hublev; // host copy of the tile ordering key
+    std::vector<int32_t> h_hublev; // host copy of the tile ordering key: hop distance to the hub
+    std::vector<int64_t> h_twohop; // ... and the arcs two hops away (tie-break)
     int tile_words = 1;           // W of the SPD kernel (unweighted graphs)
     int weighted_words = 1;       // 64-source words of a weighted tile
     int chunk_arcs = 128;
@@ -300,7 +301,7 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
                     uint32_t *qflags, unsigned long long *edges);
 bc_status check_graph(bc_graph *g, const char *fn);
 bc_status prepare_ordering(bc_graph *g);
-// Tile order of a source: hop distance to the hub, then out-degree descending.
+// Tile order of a source: hop distance to the hub, then arcs two hops away (descending).
 int64_t source_order_key(const bc_graph *g, int32_t v);
 bc_status ensure_weighted_state(bc_graph *g);
 bc_status reset_dense_state(bc_graph *g);

@@ -494,12 +494,27 @@ bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::
     return BC_OK;
 }
 
-// Tile ordering key, first part: hop distance from each vertex to the hub,
-// the vertex of largest in-degree x out-degree (one reach traversal of R(G)
-// from the hub, cached per graph). Sources at equal distance to the hub have
-// closely aligned BFS level profiles, so a tile of them touches each vertex at
-// fewer distinct levels; among them, sources of similar out-degree reach the
-// bulk of the graph at the same level (see source_order_key).
+// Sum over a vertex's out-arcs of the heads' out-degrees: the arcs two hops
+// away, a proxy of how much of the graph a BFS from the vertex reaches by its
+// second level.
+__global__ void two_hop_kernel(const int64_t *off, const int32_t *col, int32_t n, int64_t *out) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        int64_t t = 0;
+        for (int64_t a = off[v]; a < off[v + 1]; ++a) {
+            const int32_t w = col[a];
+            t += off[w + 1] - off[w];
+        }
+        out[v] = t;
+    }
+}
+
+// Tile ordering keys, cached per graph: hop distance from each vertex to the
+// hub, the vertex of largest in-degree x out-degree (one reach traversal of
+// R(G) from the hub), and the two-hop arc count. Sources at equal distance to
+// the hub have closely aligned BFS level profiles, so a tile of them touches
+// each vertex at fewer distinct levels; among them, sources of similar
+// two-hop reach reach the bulk of the graph at the same level (see
+// source_order_key).
 static bc_status ensure_hub_levels(bc_graph *g) {
     std::vector<int32_t> &h_lev = g->h_hublev;
     bcd_workspace &ws = g->ws;
@@ -531,7 +546,15 @@ static bc_status ensure_hub_levels(bc_graph *g) {
     BCD_TRY(run_traversal(g, 1, p, nullptr, nullptr));
     h_lev.resize((size_t)g->n);
     BCD_CUDA(cudaMemcpyAsync(h_lev.data(), ws.hublev, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
-    BCD_CUDA(cudaStreamSynchronize(s));
+    int64_t *d_two = nullptr;
+    BCD_TRY(dev_alloc(&d_two, (size_t)g->n));
+    two_hop_kernel<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->d_off, g->d_col, g->n, d_two);
+    g->launches += 1;
+    g->h_twohop.resize((size_t)g->n);
+    cudaError_t ce = cudaMemcpyAsync(g->h_twohop.data(), d_two, sizeof(int64_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    dev_free(d_two);
+    if (ce != cudaSuccess) return cuda_error(ce, "two-hop counts");
     ws.hub = hub;
     return BC_OK;
 }
@@ -892,10 +915,11 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
 
 int64_t source_order_key(const bc_graph *g, int32_t v) {
     if (g->source_order != 1) return v;
-    int64_t lev = 0;
-    if ((int64_t)g->h_hublev.size() == g->n) lev = g->h_hublev[v] < 0 ? 0x7fffffff : g->h_hublev[v];
-    const int64_t deg = std::min<int64_t>(g->h_off[v + 1] - g->h_off[v], 0x7fffffff);
-    return (lev << 31) | (0x7fffffff - deg);
+    constexpr int64_t kLow = ((int64_t)1 << 40) - 1;
+    int64_t lev = 0, two = 0;
+    if ((int64_t)g->h_hublev.size() == g->n) lev = g->h_hublev[v] < 0 ? ((1 << 22) - 1) : std::min(g->h_hublev[v], (1 << 22) - 2);
+    if ((int64_t)g->h_twohop.size() == g->n) two = std::min<int64_t>(g->h_twohop[v], kLow);
+    return (lev << 40) | (kLow - two);
 }
 
 bc_status prepare_ordering(bc_graph *g) { return g->source_order == 1 ? ensure_hub_levels(g) : BC_OK; }

@@ -200,7 +200,7 @@ bool bc_server::run_slice_once() {
         return false;
     }
     // tiles of sources at similar hop distance to the hub and of similar
-    // out-degree (aligned levels)
+    // two-hop reach (aligned levels)
     std::vector<size_t> order(take.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
