@@ -278,7 +278,7 @@ def run_gpu(args):
     algo_bytes = 2.0 * (8.0 * vb + 4.0 * eb) + 40.0 * reached + 24.0 * tight
     peak, peak_kind = peaks()
     achieved = algo_bytes / (trav_ms / 1000.0) / 1e9
-    tb = TRAFFIC_BYTES_PER_EDGE.get(args.workload) if args.tile_words == 2 else None
+    tb = TRAFFIC_BYTES_PER_EDGE.get(args.workload) if args.tile_words == 4 else None
     traffic = None if tb is None else tb * edges
 
     # end to end through the C ABI: pinned host CSR in, results out
@@ -534,7 +534,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--tile-words", type=int, default=2)
+    ap.add_argument("--tile-words", type=int, default=4)
     ap.add_argument("--cpu-sources", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="", choices=["", "profile", "wprofile"],

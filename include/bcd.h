@@ -285,7 +285,9 @@ void bc_server_destroy(bc_server *srv);
  * Tuning of the batched traversal (no effect on results beyond fp64
  * summation order of delta):
  *   tile_words     mask words per tile: 1, 2 or 4 (64, 128 or 256 sources
- *                  advanced together);
+ *                  advanced together; bc_graph_create picks the widest
+ *                  whose sigma and accumulator slabs, 16 bytes per (vertex,
+ *                  source) pair, fit in half of the free device memory);
  *   chunk_arcs     arcs per unit of work when a vertex's row is split
  *                  (32..65536, a multiple of 32);
  *   block_threads  threads per block of the persistent kernel (128..512,
@@ -296,8 +298,8 @@ void bc_server_destroy(bc_server *srv);
  *                  arcs two hops away (largest first), so that a tile's BFS
  *                  levels line up;
  *                  2 keeps ascending vertex ids;
- *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2
- *                  trades register spills for occupancy);
+ *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2,
+ *                  the default, trades register spills for occupancy);
  *   weighted_words sources per tile of the weighted kernel, in words of 64
  *                  (1, 2, 4, 8 or 16, with n * 64 * weighted_words <= 2^32).
  *                  bc_graph_create picks the widest that fits in half of

@@ -273,6 +273,21 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
     if (ce != cudaSuccess) return fail(cuda_error(ce, "build reverse graph"));
     if ((ce = cudaGetLastError()) != cudaSuccess) return fail(cuda_error(ce, "graph kernels"));
     g->launches += 5;
+    if (!g->weighted) {
+        // widest unweighted tile (up to 256 sources) whose per-pair state
+        // (sigma and accumulator slabs, 16 bytes per (vertex, source) pair)
+        // fits in half of the free device memory; 4-word tiles run two blocks
+        // per SM
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        int w = 4;
+        while (w > 1 && (double)d->n * 64.0 * w * 16.0 > 0.5 * (double)fr) w >>= 1;
+        g->tile_words = w;
+        g->blocks_per_sm = 2;
+    }
     if (g->weighted) {
         // widest weighted tile (up to 1024 sources) whose per-pair state
         // (dist, sigma, history, bucket share: about 40 bytes) fits in half of

@@ -86,7 +86,8 @@ def test_probe_dist_sigma_delta(bcd, er1, tile_words):
             assert close(dep[i, j], st["delta"][t]), (s, t, dep[i, j], st["delta"][t])
 
 
-@pytest.mark.parametrize("cfg", [{}, {"tile_words": 2}, {"tile_words": 4}, {"chunk_arcs": 32},
+@pytest.mark.parametrize("cfg", [{}, {"tile_words": 1}, {"tile_words": 2}, {"tile_words": 4, "blocks_per_sm": 1},
+                                 {"tile_words": 4, "blocks_per_sm": 2}, {"chunk_arcs": 32},
                                  {"block_threads": 256, "chunk_arcs": 64}])
 def test_exact_matches_oracle(bcd, er1, cfg):
     g, og = er1

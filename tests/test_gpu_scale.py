@@ -1,5 +1,5 @@
 """Parity at full size, in the launch configuration bench.py times (tiles of
-128 sources, 128-arc chunks, hub-distance tile order).
+256 sources at two blocks per SM, 128-arc chunks, default tile order).
 
 R-MAT scale 20 (the exact batch): RV lists of all 64 queries bit-exact;
 dist and sigma of sampled union sources bit-exact and their dependencies on
@@ -40,7 +40,7 @@ def rmat20(bcd):
     g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
     qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    bcd.bc_set_config(dg, tile_words=2, chunk_arcs=128)
+    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2)
     return g, O.Graph.from_csr(g), dg, qs
 
 
@@ -91,7 +91,7 @@ def test_rmat20_small_queries_full(bcd, rmat20):
 def rmat22(bcd):
     g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    bcd.bc_set_config(dg, tile_words=2, chunk_arcs=128)
+    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2)
     return g, O.Graph.from_csr(g), dg
 
 
