@@ -37,10 +37,10 @@ METRIC = "GTEPS and BC(r) queries/s (exact and sampled) vs HBM roofline; p50/p99
 WORKLOAD = "rmat20_ef16_exact64"
 # dram bytes per (source x reached arc) of the traversal kernel, per workload
 # graph, from the ncu capture summarised in
-# profiles/trav_kernel_rmat20_sampled512_w2.md (R-MAT scale 20, 128-source
-# tiles); a workload without an entry, or a kernel changed since the capture,
-# reports traffic null
-TRAFFIC_BYTES_PER_EDGE = {}
+# profiles/trav_kernel_rmat20_sampled512_w4.md (R-MAT scale 20, 256-source
+# tiles); a workload without an entry, another tile width, or a kernel changed
+# since the capture, reports traffic null
+TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 10.03}
 
 
 def log(*a):
