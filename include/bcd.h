@@ -302,9 +302,10 @@ void bc_server_destroy(bc_server *srv);
  *                  the default, trades register spills for occupancy);
  *   weighted_words sources per tile of the weighted kernel, in words of 64
  *                  (1, 2, 4, 8 or 16, with n * 64 * weighted_words <= 2^32).
- *                  bc_graph_create picks the widest that fits in half of
- *                  the free device memory at about 40 bytes per (vertex,
- *                  source) pair. tile_words applies to unweighted graphs only.
+ *                  bc_graph_create picks 4, or less when that does not fit
+ *                  in half of the free device memory at about 40 bytes per
+ *                  (vertex, source) pair. tile_words applies to unweighted
+ *                  graphs only.
  * Zero fields keep their current value.
  */
 typedef struct {

@@ -289,15 +289,17 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
         g->blocks_per_sm = 2;
     }
     if (g->weighted) {
-        // widest weighted tile (up to 1024 sources) whose per-pair state
-        // (dist, sigma, history, bucket share: about 40 bytes) fits in half of
-        // the free device memory, with vertex << log2(S) in 32 bits
+        // weighted tile of up to 256 sources (wider tiles measured no faster:
+        // sources rarely share a distance, so the work per level grows with
+        // the tile), narrower when its per-pair state (dist, sigma, history,
+        // bucket share: about 40 bytes) does not fit in half of the free device
+        // memory; vertex << log2(S) must fit in 32 bits
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
             cudaGetLastError();
             fr = 0;
         }
-        int nw = 16;
+        int nw = 4;
         while (nw > 1 && ((((uint64_t)d->n) << 6) * (uint64_t)nw > (1ull << 32) ||
                           (double)d->n * 64.0 * nw * 40.0 > 0.5 * (double)fr))
             nw >>= 1;

@@ -497,14 +497,19 @@ bc_status build_rv_lists(bc_graph *g, const std::vector<int> &slots, const std::
 // Sum over a vertex's out-arcs of the heads' out-degrees: the arcs two hops
 // away, a proxy of how much of the graph a BFS from the vertex reaches by its
 // second level.
+// One warp per vertex (lanes over its arcs), so hub rows do not hold a thread.
 __global__ void two_hop_kernel(const int64_t *off, const int32_t *col, int32_t n, int64_t *out) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nw) {
         int64_t t = 0;
-        for (int64_t a = off[v]; a < off[v + 1]; ++a) {
+        for (int64_t a = off[v] + lane; a < off[v + 1]; a += 32) {
             const int32_t w = col[a];
             t += off[w + 1] - off[w];
         }
-        out[v] = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[v] = t;
     }
 }
 
@@ -548,7 +553,7 @@ static bc_status ensure_hub_levels(bc_graph *g) {
     BCD_CUDA(cudaMemcpyAsync(h_lev.data(), ws.hublev, sizeof(int32_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s));
     int64_t *d_two = nullptr;
     BCD_TRY(dev_alloc(&d_two, (size_t)g->n));
-    two_hop_kernel<<<grid_for(g, g->n, 256), 256, 0, s>>>(g->d_off, g->d_col, g->n, d_two);
+    two_hop_kernel<<<grid_for(g, (int64_t)g->n * 32, 256), 256, 0, s>>>(g->d_off, g->d_col, g->n, d_two);
     g->launches += 1;
     g->h_twohop.resize((size_t)g->n);
     cudaError_t ce = cudaMemcpyAsync(g->h_twohop.data(), d_two, sizeof(int64_t) * (size_t)g->n, cudaMemcpyDeviceToHost, s);

@@ -140,7 +140,7 @@ def test_rmat20_weighted_rv_lists(bcd, rmat20w):
 
 def test_rmat20_weighted_sampled_sources(bcd, rmat20w):
     g, og, dg, qs = rmat20w
-    assert bcd.bc_get_config(dg)["weighted_words"] == 16
+    assert bcd.bc_get_config(dg)["weighted_words"] == 4
     sizes = {r: bcd.bc_rv_compute(dg, r).shape[0] for r in dict.fromkeys(qs)}
     big = max(sizes, key=sizes.get)
     union = O.rv(og, big)
