@@ -53,7 +53,7 @@ struct __align__(16) Chunk {
     int32_t nch;
     int64_t a0;
     int32_t na;
-    int32_t pad;   // kind: 0 out-arcs, 1 in-arcs (weighted sigma pull)
+    int32_t pad;   // unweighted out-arc chunks: the row's length; weighted: kind (0 out, 1 in) | source << 1
 };
 
 // Traversal modes of the persistent kernel.

@@ -127,14 +127,15 @@ __device__ __forceinline__ void store_chunk(Chunk *c, int v, int e, int k, int n
     d[1] = make_int4((int)(unsigned)(a0 & 0xffffffffll), (int)(unsigned)((unsigned long long)a0 >> 32), na, kind);
 }
 
-// Writes the chunk descriptors of a vertex with arcs [rb, re).
+// Writes the chunk descriptors of a vertex with arcs [rb, re); the last
+// field carries the row's length (the vertex's out-degree).
 __device__ __forceinline__ void emit_chunks(const TravParams &p, long long c0, int v, int e, int nch, long long rb,
                                             long long re) {
     const int CH = p.chunk_arcs;
     for (int kk = 0; kk < nch; ++kk) {
         const long long a0 = rb + (long long)kk * CH;
         const long long a1 = min(re, a0 + CH);
-        store_chunk(&p.chunks[c0 + kk], v, e, kk, nch, a0, (int)max(0ll, a1 - a0));
+        store_chunk(&p.chunks[c0 + kk], v, e, kk, nch, a0, (int)max(0ll, a1 - a0), (int)(re - rb));
     }
 }
 

@@ -213,17 +213,17 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
 #pragma unroll
             for (int w = 0; w < W; ++w)
                 if (lane == w) p.hm[(size_t)e * W + w] = F[w];
-            if (lane == 0) {
-                uint64_t *vis = p.vs + (size_t)v * stride;
+            // visited |= F: reductions that need no answer (the sources of F are
+            // already excluded from new bits by the current-level mask)
 #pragma unroll
-                for (int w = 0; w < W; ++w) vis[w] |= F[w];
-            }
+            for (int w = 0; w < W; ++w)
+                if (lane == w) atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + w], (unsigned long long)F[w]);
             if (MODE == kModeSpd) {
                 if (lane == 0) {
                     int pc = 0;
 #pragma unroll
                     for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
-                    st.edges += (unsigned)pc * (unsigned)(p.off[v + 1] - p.off[v]);
+                    st.edges += (unsigned)pc * (unsigned)ch.pad;  // out-degree of v rides in the chunk
                     st.reached += (unsigned)pc;
                 }
                 const uint64_t qm = p.qmask[v];
