@@ -139,6 +139,40 @@ __device__ __forceinline__ void emit_chunks(const TravParams &p, long long c0, i
     }
 }
 
+// Per-query partial sums of a tile's dependencies (one block): eight threads
+// per query, each over every eighth source slot, combined by a fixed shuffle
+// tree, so the order does not depend on scheduling. The multiplicity of a
+// source is 1 (exact queries: the query needs it) or its draw count.
+__device__ inline void tile_query_sums(const TravParams &p, long long tile, int S, const int32_t *tsrc,
+                                       const uint64_t *s_need) {
+    for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
+        const int q = t >> 3, j = t & 7;
+        const bool exact = (p.exact_q >> q) & 1ull;
+        double sum = 0.0;
+        int flagged = 0;
+        for (int s = j; s < S; s += 8) {
+            if (tsrc[s] < 0) continue;
+            double mlt = 0.0;
+            if (exact)
+                mlt = ((s_need[s] >> q) & 1ull) ? 1.0 : 0.0;
+            else if (p.mult)
+                mlt = (double)p.mult[((size_t)tile * S + s) * 64 + q];
+            if (mlt != 0.0) {
+                sum += mlt * p.dep[s * 64 + q];
+                if ((p.srcflag[s >> 6] >> (s & 63)) & 1ull) flagged = 1;
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            sum += __shfl_down_sync(kFull, sum, o, 8);
+            flagged |= __shfl_down_sync(kFull, flagged, o, 8);
+        }
+        if (j == 0) {
+            p.tile_partial[tile * 64 + q] = sum;
+            if (flagged) p.qflags[q] |= 1u;
+        }
+    }
+}
 
 }  // namespace dev
 }  // namespace bcd

@@ -508,26 +508,7 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
         wflush(p.ctr, st, lane);
 
         // ---------------- tile end ----------------
-        if (blockIdx.x == 0 && threadIdx.x < 64) {
-            const int q = threadIdx.x;
-            const bool exact = (p.exact_q >> q) & 1ull;
-            double sum = 0.0;
-            bool flagged = false;
-            for (int s = 0; s < S; ++s) {
-                if (tsrc[s] < 0) continue;
-                double mlt = 0.0;
-                if (exact)
-                    mlt = ((s_need[s] >> q) & 1ull) ? 1.0 : 0.0;
-                else if (p.mult)
-                    mlt = (double)p.mult[((size_t)tile * S + s) * 64 + q];
-                if (mlt != 0.0) {
-                    sum += mlt * p.dep[s * 64 + q];
-                    if ((p.srcflag[s >> 6] >> (s & 63)) & 1ull) flagged = true;
-                }
-            }
-            p.tile_partial[tile * 64 + q] = sum;
-            if (flagged) p.qflags[q] |= 1u;
-        }
+        if (blockIdx.x == 0) tile_query_sums(p, tile, S, tsrc, s_need);
         if (!(p.flags & kFlagNoReset)) {
             for (long long e = gthr; e < total; e += nthr) {
                 const int v = p.hv[e];
