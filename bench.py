@@ -40,7 +40,7 @@ WORKLOAD = "rmat20_ef16_exact64"
 # profiles/trav_kernel_rmat20_sampled512_w4.md (R-MAT scale 20, 256-source
 # tiles); a workload without an entry, another tile width, or a kernel changed
 # since the capture, reports traffic null
-TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 10.03}
+TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 10.02}
 
 
 def log(*a):
