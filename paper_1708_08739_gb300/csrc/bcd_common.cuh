@@ -19,7 +19,6 @@ enum DevErr : int32_t {
     kDevOk = 0,
     kDevHistOverflow = 1,
     kDevChunkOverflow = 2,
-    kDevSlotOverflow = 3,
     kDevTimeout = 4,
     kDevLevelOverflow = 5,
     kDevBucketOverflow = 6,
@@ -32,7 +31,6 @@ struct Counters {
     uint32_t bar_gen;
     uint32_t pad0;
     unsigned long long edges;      // sum over reached (v, s) of out-degree(v)
-    unsigned long long pslots;     // partial-row slots handed out this tile
     unsigned long long levels_max; // deepest level met over all tiles
     unsigned long long ns_fwd;     // block 0's wall time in forward passes
     unsigned long long ns_bwd;     // ... in backward passes
@@ -87,7 +85,6 @@ struct TravParams {
     int32_t *hv;        // [hcap]
     uint64_t *hm;       // [hcap * W] (unweighted)
     uint16_t *hs;       // [hcap] source slot of an entry (weighted)
-    int64_t *hslot;     // [hcap]
     int64_t hcap;
     Chunk *chunks;      // [ccap]
     Chunk *ichunks;     // [ccap] in-arc (R(G)) chunks of the entries, per level (unweighted SPD)
@@ -156,7 +153,6 @@ struct bcd_workspace {
     uint64_t *hm = nullptr;
     int64_t hmcap = 0;            // entries hm holds (hcap but on weighted graphs)
     uint16_t *hs = nullptr;
-    int64_t *hslot = nullptr;
     int64_t hcap = 0;
     bcd::Chunk *chunks = nullptr;
     bcd::Chunk *ichunks = nullptr;

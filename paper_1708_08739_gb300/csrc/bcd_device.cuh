@@ -1,5 +1,5 @@
 // Device helpers shared by the traversal kernels: bounded grid barrier,
-// chunk descriptors and their dynamic hand-out, asynchronous copies.
+// chunk descriptors and their dynamic hand-out, per-query tile sums.
 #pragma once
 
 #include "bcd_common.cuh"
@@ -92,19 +92,6 @@ struct ChunkGrabber {
         return true;
     }
 };
-
-// Bytes of shared memory each warp stages backward gathers in.
-constexpr int kStageBytes = 4096;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 __device__ __forceinline__ Chunk load_chunk(const Chunk *c) {
     const int4 a = reinterpret_cast<const int4 *>(c)[0];

@@ -174,7 +174,6 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     dev_free(ws.hv);
     dev_free(ws.hm);
     dev_free(ws.hs);
-    dev_free(ws.hslot);
     dev_free(ws.chunks);
     dev_free(ws.ichunks);
     dev_free(ws.partial);
@@ -190,7 +189,6 @@ static bc_status alloc_history(bc_graph *g, int64_t hcap, int64_t ccap, int64_t 
     BCD_TRY(dev_alloc(&ws.hv, (size_t)hcap));
     BCD_TRY(dev_alloc(&ws.hm, wg ? (size_t)hmcap : (size_t)hcap * ws.W));
     BCD_TRY(dev_alloc(&ws.hs, wg ? (size_t)hcap : (size_t)1));
-    BCD_TRY(dev_alloc(&ws.hslot, (size_t)1));
     BCD_TRY(dev_alloc(&ws.chunks, (size_t)ccap));
     BCD_TRY(dev_alloc(&ws.ichunks, wg ? (size_t)1 : (size_t)ccap));
     BCD_TRY(dev_alloc(&ws.partial, wg ? (size_t)pcap : (size_t)1));
@@ -289,7 +287,6 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.hv);
     dev_free(ws.hm);
     dev_free(ws.hs);
-    dev_free(ws.hslot);
     dev_free(ws.chunks);
     dev_free(ws.ichunks);
     dev_free(ws.partial);

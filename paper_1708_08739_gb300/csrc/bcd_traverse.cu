@@ -650,7 +650,6 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                     p.lev_grab[p.maxlev + 2 + l] = 0ull;
                     p.lev_grab[2 * (p.maxlev + 2) + l] = 0ull;
                 }
-                if (threadIdx.x == 0) p.ctr->pslots = 0ull;
             }
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
@@ -715,7 +714,6 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.rcol = g->d_rcol;
         p.hv = ws.hv;
         p.hm = ws.hm;
-        p.hslot = ws.hslot;
         p.hcap = p.mode == kModeReach ? ws.hmcap : ws.hcap;
         p.chunks = ws.chunks;
         p.ichunks = ws.ichunks;
