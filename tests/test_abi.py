@@ -57,3 +57,42 @@ def test_no_oracle_in_product_path():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "bc_oracle" not in src and "liboracle" not in src, f
+
+
+STRUCTS = ["bc_graph_desc", "bc_info", "bc_query", "bc_result", "bc_batch_info", "bc_config", "bc_server_config",
+           "bc_server_stats"]
+
+
+def test_binding_struct_layouts_match_the_header(built_lib, tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets, as a C compiler lays them out (gcc on the header itself)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "bcd.h"', "int main(void) {"]
+    for name in STRUCTS:
+        py = getattr(built_lib, name)
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line.strip():
+            continue
+        name, field, value = line.split()
+        py = getattr(built_lib, name)
+        if field == "size":
+            assert ctypes.sizeof(py) == int(value), name
+        else:
+            assert getattr(py, field).offset == int(value), (name, field)
+        seen += 1
+    assert seen == sum(1 + len(getattr(built_lib, n)._fields_) for n in STRUCTS)
