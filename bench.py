@@ -36,11 +36,12 @@ import graphgen as gg  # noqa: E402
 METRIC = "GTEPS and BC(r) queries/s (exact and sampled) vs HBM roofline; p50/p99 query latency"
 WORKLOAD = "rmat20_ef16_exact64"
 # dram bytes per (source x reached arc) of the traversal kernel, per workload,
-# from the ncu captures summarised in profiles/trav_kernel_rmat20_sampled512_w4.md
-# (R-MAT scale 20) and profiles/trav_kernel_rmat22_recip30_sampled64_w4.md (the
-# full R-MAT scale 22 launch), 256-source tiles; a workload without an entry,
-# another tile width, or a kernel changed since the capture, reports traffic null
-TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 10.02, "rmat22_ef8_recip30_sampled64": 12.33}
+# from one-pass ncu captures of each workload's full launch, summarised in
+# profiles/trav_kernel_rmat20_exact64_w4.md and
+# profiles/trav_kernel_rmat22_recip30_sampled64_w4.md (256-source tiles); a
+# workload without an entry, another tile width, or a kernel changed since the
+# capture, reports traffic null
+TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 9.42, "rmat22_ef8_recip30_sampled64": 12.33}
 
 
 def log(*a):
