@@ -447,16 +447,19 @@ def run_serve(args):
 
 def run_profile_case(args):
     """A small launch of the same traversal kernel for ncu captures: one
-    sampled query (T = args.case_T draws, seed 7) on the R-MAT 20 graph."""
+    sampled query (T = args.case_T draws, seed 7) on the R-MAT 20 graph, with
+    the Eq. 4 backward of the batched kernel (--accumulation 2: the vertex
+    scan)."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1708_08739_gb300 as bcd
     g, qs, _ = make_workload()
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    bcd.bc_set_config(dg, tile_words=args.tile_words, accumulation=args.accumulation or 1)
     r = int(gg.top_inout_vertices(g, 1)[0])
     out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
-    print(json.dumps({"case": "profile", "r": r, "T": args.case_T, "bc": out[0]["bc"], "info": info}), flush=True)
+    print(json.dumps({"case": "profile", "r": r, "T": args.case_T, "bc": out[0]["bc"],
+                      "accumulation": bcd.bc_get_config(dg)["accumulation"], "info": info}), flush=True)
     dg.close()
 
 
@@ -478,6 +481,59 @@ def run_wprofile_case(args):
     print(json.dumps({"case": "wprofile", "scale": args.case_scale, "r": r, "T": args.case_T, "bc": out[0]["bc"],
                       "config": bcd.bc_get_config(dg), "info": info}), flush=True)
     dg.close()
+
+
+def run_single(args):
+    """Single-query latency, one query per bc_batch call, under both
+    accumulations: 1 (the backward pass of Eq. 4, pushed along tight in-arcs)
+    and 2 (the vertex scan after a traversal from r). Queries: A-BCD with
+    eps 0.01, delta 0.1 (T = 14,979, seed 7) on the R-MAT 20 vertex of largest
+    in-degree x out-degree and on the first uniform query (seed 105) of the
+    R-MAT 22 graph with 30 % reciprocal arcs whose |RV| exceeds 1000. One
+    warm-up call, then args.single_reps timed calls per accumulation (wall
+    clock around the synchronous call; CUDA-event phase times from the batch
+    report). Prints one JSON line per (graph, accumulation)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    import paper_1708_08739_gb300 as bcd
+    cases = []
+    g20, _, _ = make_workload("rmat20_ef16_exact64")
+    cases.append(("rmat20_ef16", g20, int(gg.top_inout_vertices(g20, 1)[0])))
+    g22, qs22, _ = make_workload("rmat22_ef8_recip30_sampled64")
+    cases.append(("rmat22_ef8_recip30", g22, None))
+    for name, g, r in cases:
+        dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+        bcd.bc_set_config(dg, tile_words=args.tile_words)
+        if r is None:
+            r = next(q for q in qs22 if bcd.bc_rv_compute(dg, q).shape[0] > 1000)
+        spec = {"r": r, "kind": bcd.BC_QUERY_APPROX, "eps": 0.01, "delta": 0.1, "seed": 7}
+        for acc in (1, 2):
+            bcd.bc_set_config(dg, accumulation=acc)
+            out, _ = bcd.bc_batch(dg, [spec])
+            torch.cuda.synchronize()
+            clk = ClockSampler(torch.cuda.current_device())
+            clk.start()
+            walls, infos = [], []
+            for _ in range(args.single_reps):
+                t = time.perf_counter()
+                out, info = bcd.bc_batch(dg, [spec])
+                walls.append(1000.0 * (time.perf_counter() - t))
+                infos.append(info)
+            clocks = clk.stop()
+            med = float(np.median(walls))
+            keys = ("ms_total", "ms_rv", "ms_sample", "ms_spd", "ms_traversal", "ms_root", "ms_forward",
+                    "ms_backward")
+            phases = {k: float(np.median([i[k] for i in infos])) for k in keys}
+            line = {"case": "single", "graph": name, "r": r, "T": out[0]["samples"], "rv_size": out[0]["rv_size"],
+                    "accumulation": acc, "bc": out[0]["bc"], "ms_per_query_median": med,
+                    "ms_per_query_min": min(walls), "queries_per_s": 1000.0 / med, "reps": len(walls),
+                    "phases_ms_median": phases, "sources_run": infos[-1]["sources_run"],
+                    "tiles": infos[-1]["tiles"], "scan_pairs": infos[-1]["scan_pairs"],
+                    "reached_pairs": infos[-1]["reached_pairs"], "tight_pairs": infos[-1]["tight_pairs"],
+                    "clocks": clocks}
+            print(json.dumps(line), flush=True)
+        dg.close()
 
 
 def run_set_experiment(args):
@@ -548,6 +604,11 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
     ap.add_argument("--set-experiment", action="store_true",
                     help="the set experiment of Section 5 (sets of 5, 10, 15 vertices, tau = 1000)")
+    ap.add_argument("--single", action="store_true",
+                    help="single-query latency under both accumulations (Eq. 4 push, vertex scan)")
+    ap.add_argument("--single-reps", type=int, default=5)
+    ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2],
+                    help="profile case: 1 Eq. 4 backward (the case's default), 2 vertex scan")
     ap.add_argument("--serve-queries", type=int, default=256)
     ap.add_argument("--serve-rv-max", type=int, default=100000)
     args = ap.parse_args()
@@ -556,6 +617,8 @@ def main():
         args.warmup = 3
     if args.serve:
         run_serve(args)
+    elif args.single:
+        run_single(args)
     elif args.set_experiment:
         run_set_experiment(args)
     elif args.case == "profile":

@@ -40,6 +40,7 @@ struct Counters {
     unsigned long long arc_visits; // arcs scanned, forward plus backward
     unsigned long long vb;         // sum over tiles of distinct vertices reached
     unsigned long long eb;         // sum over tiles of the out-arcs of those vertices
+    unsigned long long vpairs;     // vertex scan: (t, s) pairs with the query vertex on a shortest s-t path
 };
 
 // One unit of expansion work: arcs [a0, a0 + na) of vertex v, the k-th of
@@ -57,7 +58,8 @@ struct __align__(16) Chunk {
 // Traversal modes of the persistent kernel.
 enum TravMode : int32_t {
     kModeReach = 0,  // masks only (RV on R(G)); no sigma, no backward
-    kModeSpd = 1,    // sigma forward, dependency backward
+    kModeSpd = 1,    // sigma forward, dependency backward (Eq. 4)
+    kModeScan = 2,   // sigma forward, dependencies on one query vertex by a vertex scan
 };
 
 // Flags of a traversal launch.
@@ -65,6 +67,7 @@ enum TravFlags : int32_t {
     kFlagNoBackward = 1,   // stop after the forward pass
     kFlagNoReset = 2,      // leave the dense state dirty (probe export)
     kFlagFullBackward = 4, // backward down to level 0 for every source
+    kFlagRootOut = 8,      // scan mode: write the level and sigma of source slot 0 to rlev / rsig
 };
 
 struct TravParams {
@@ -125,6 +128,12 @@ struct TravParams {
     int32_t ring;            // power of two above the largest weight
     int32_t nw;              // 64-source words of a weighted tile (1, 2, 4, 8 or 16)
     int64_t *lev_dist;       // [maxlev + 2] distance of each non-empty level
+    // vertex scan (one query vertex vroot): its forward traversal and per-source sums
+    int32_t *rlev;           // [n] d(vroot, t), -1 unreached
+    double *rsig;            // [n] sigma from vroot to t
+    double *vsum;            // [S] sigma_s(vroot) * sum_t sigma_rt / sigma_st of the current tile
+    int32_t vroot;
+    int32_t pad2;
     // reach mode output
     uint64_t *rvmask;        // [n]
     int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
@@ -184,6 +193,10 @@ struct bcd_workspace {
     int32_t *dlist = nullptr;     // [n + 64 * W + 256] source union, padded to whole tiles
     int32_t *qlevel = nullptr;    // [64 * W * 64]
     double *dep = nullptr;        // [64 * W * 64]
+    int32_t *rlev = nullptr;      // [n] vertex scan: levels from the query vertex (unweighted graphs)
+    double *rsig = nullptr;       // [n] ... and its path counts
+    double *vsum = nullptr;       // [64 * W] ... and the per-source sums of a tile
+    int32_t *rtile = nullptr;     // [64 * W] the one-source tile of the query vertex's traversal
     uint32_t *qflags = nullptr;   // [64]
     uint64_t *srcflag = nullptr;  // [W]
     bcd::Counters *ctr = nullptr;
@@ -238,6 +251,7 @@ struct bc_graph {
     int source_order = 1;         // 1: tiles ordered by distance to the hub, 0: by vertex id
     int blocks_per_sm = 1;        // resident blocks per SM of the 256-source kernel (1 or 2)
     int block_threads = 512;
+    int accumulation = 2;         // 1: Eq. 4 push, 2: vertex scan for launches with one query vertex
     bcd_workspace ws;
     int64_t launches = 0;
     int last_grid = 0;                       // blocks of the last traversal launch

@@ -143,6 +143,16 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
             return set_error(BC_E_INVALID_ARG, "bc_set_config: weighted_words must be 1, 2, 4, 8 or 16 with n * 64 * weighted_words <= 2^32");
         g->weighted_words = w;
     }
+    {
+        // the unweighted kernel seeds a tile's S = 64 * tile_words sources with one thread each
+        const int tw = c->tile_words ? c->tile_words : g->tile_words;
+        const int bt = c->block_threads ? c->block_threads : g->block_threads;
+        if (!g->weighted && bt < 64 * tw)
+            return set_error(BC_E_INVALID_ARG, "bc_set_config: block_threads must be at least 64 * tile_words");
+    }
+    if (c->accumulation && c->accumulation != 1 && c->accumulation != 2)
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: accumulation must be 1 or 2");
+    if (c->accumulation) g->accumulation = c->accumulation;
     if (c->tile_words) g->tile_words = c->tile_words;
     if (c->chunk_arcs) g->chunk_arcs = c->chunk_arcs;
     if (c->block_threads) g->block_threads = c->block_threads;
@@ -157,7 +167,8 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->source_order = g->source_order == 1 ? 1 : 2;
     c->blocks_per_sm = g->blocks_per_sm;
     c->weighted_words = g->weighted_words;
-    c->reserved[0] = c->reserved[1] = 0;
+    c->accumulation = g->accumulation;
+    c->reserved = 0;
     return BC_OK;
 }
 

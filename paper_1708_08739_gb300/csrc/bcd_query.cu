@@ -309,6 +309,10 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.dlist);
     dev_free(ws.qlevel);
     dev_free(ws.dep);
+    dev_free(ws.rlev);
+    dev_free(ws.rsig);
+    dev_free(ws.vsum);
+    dev_free(ws.rtile);
     dev_free(ws.qflags);
     dev_free(ws.srcflag);
     dev_free(ws.ctr);
@@ -350,6 +354,12 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 64 * (size_t)W + 256));  // union padded to whole tiles
     BCD_TRY(dev_alloc(&ws.qlevel, (size_t)64 * W * 64));
     BCD_TRY(dev_alloc(&ws.dep, (size_t)64 * W * 64));
+    if (!g->weighted) {  // vertex scan state
+        BCD_TRY(dev_alloc(&ws.rlev, (size_t)n));
+        BCD_TRY(dev_alloc(&ws.rsig, (size_t)n));
+        BCD_TRY(dev_alloc(&ws.vsum, (size_t)64 * W));
+        BCD_TRY(dev_alloc(&ws.rtile, (size_t)64 * W));
+    }
     BCD_TRY(dev_alloc(&ws.qflags, 64));
     BCD_TRY(dev_alloc(&ws.srcflag, (size_t)std::max(W, 4)));
     BCD_TRY(dev_alloc(&ws.ctr, 1));
@@ -395,7 +405,7 @@ struct GQuery {
 
 struct GroupTimes {
     float rv = 0, sample = 0, spd = 0, total = 0;
-    double fwd = 0, bwd = 0, trav = 0;
+    double fwd = 0, bwd = 0, trav = 0, root = 0;
     bcd::Counters c{};
     int64_t sources = 0;
     int64_t tiles = 0;
@@ -583,6 +593,48 @@ static bc_status order_sources(bc_graph *g, int64_t nd) {
 static double samples_for(double eps, double delta) { return std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps)); }
 
 // Runs one group of at most 64 queries whose out-degree is positive.
+// d(r, t) and sigma_rt for every vertex t (the forward pass of Section 2 from
+// r alone), kept in rlev / rsig for the vertex scan: a scan-mode launch over
+// one tile whose only source is r. Its tile sums are not used (no query takes
+// slot 0: exact_q is 0 and there are no draw counts).
+static bc_status root_traversal(bc_graph *g, int32_t r) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int W = tile_words_of(g);
+    const int S = 64 * W;
+    fill_i32<<<1, 256, 0, s>>>(ws.rtile, S, -1);
+    fill_i32<<<1, 32, 0, s>>>(ws.rtile, 1, r);
+    g->launches += 2;
+    BCD_CUDA(cudaMemsetAsync(ws.rlev, 0xff, sizeof(int32_t) * (size_t)g->n, s));
+    BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, 64));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeScan;
+    p.flags = kFlagRootOut;
+    p.off = g->d_off;
+    p.col = g->d_col;
+    p.srcs = ws.rtile;
+    p.ntiles = 1;
+    p.qmask = ws.qmask;
+    p.need = ws.need;
+    p.exact_q = 0;
+    p.mult = nullptr;
+    p.qlevel = ws.qlevel;
+    p.dep = ws.dep;
+    p.tile_partial = ws.tile_partial;
+    p.qflags = ws.qflags;
+    p.srcflag = ws.srcflag;
+    p.rlev = ws.rlev;
+    p.rsig = ws.rsig;
+    p.vsum = ws.vsum;
+    p.vroot = r;
+    return run_traversal(g, W, p, nullptr, nullptr);
+}
+
+static bool use_vertex_scan(const bc_graph *g, size_t nroots) {
+    return g->accumulation == 2 && !g->weighted && nroots == 1;
+}
+
 static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
@@ -694,12 +746,23 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     std::vector<uint32_t> qflags(64, 0);
     int levels = 0;
     unsigned long long edges = 0;
+    const bool scan = ntiles > 0 && use_vertex_scan(g, roots.size());
+    if (scan) {
+        BCD_TRY(root_traversal(g, roots[0]));
+        tm.root = g->last_ms_launch;
+    }
     if (ntiles > 0) {
         BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, ntiles * 64));
         TravParams p;
         memset(&p, 0, sizeof(p));
-        p.mode = kModeSpd;
+        p.mode = scan ? kModeScan : kModeSpd;
         p.flags = 0;
+        if (scan) {
+            p.rlev = ws.rlev;
+            p.rsig = ws.rsig;
+            p.vsum = ws.vsum;
+            p.vroot = roots[0];
+        }
         p.off = g->d_off;
         p.col = g->d_col;
         p.srcs = ws.dlist;
@@ -968,6 +1031,8 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.arc_visits += (int64_t)t.c.arc_visits;
         bi.union_vertices += (int64_t)t.c.vb;
         bi.union_arcs += (int64_t)t.c.eb;
+        bi.scan_pairs += (int64_t)t.c.vpairs;
+        bi.ms_root += t.root;
         group.clear();
         return BC_OK;
     };

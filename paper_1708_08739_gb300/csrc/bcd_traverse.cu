@@ -20,6 +20,12 @@
 //            hold the warp; after a barrier the level-L entries turn acc
 //            into delta and c. The sum order follows the schedule, so delta
 //            can differ from run to run in its last bits.
+// Scan mode (every query of the launch at one vertex r) keeps the forward
+//            pass and replaces the backward by one pass over the reached
+//            (vertex, source) pairs: delta_s.(r) = sigma_sr * sum of
+//            sigma_rt / sigma_st over the t behind r on a shortest s-t path,
+//            with d(r, t) and sigma_rt from an earlier scan-mode launch whose
+//            only source is r (kFlagRootOut).
 // Reach mode (RV(r), Section 4.1) runs the forward pass only, over R(G),
 // with one source slot per query root, and ORs every level mask into rvmask.
 //
@@ -92,7 +98,8 @@ __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app
     }
 }
 
-// Level 0 of a tile: one entry per source slot (block 0 only).
+// Level 0 of a tile: one entry per source slot (block 0 only). Thread t
+// seeds slot t: the launch has at least S threads per block.
 template <int W, int MODE>
 __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
     constexpr int S = 64 * W;
@@ -135,17 +142,18 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
             p.hv[t] = v;
             p.tag[v] = 0;
             emit_chunks(p, c0, v, t, nch, rb, re);
-            if (MODE == kModeSpd) {
+            if (MODE != kModeReach) {
                 atomicAdd(&p.ctr->vb, 1ull);
                 atomicAdd(&p.ctr->eb, (unsigned long long)(re - rb));
             }
-            if (MODE == kModeSpd) p.sigma[(size_t)v * S + t] = 1.0;
+            if (MODE != kModeReach) p.sigma[(size_t)v * S + t] = 1.0;
         }
     }
-    if (MODE == kModeSpd) {
+    if (MODE != kModeReach) {
         for (int i = t; i < S * 64; i += blockDim.x) p.qlevel[i] = -1;
         if (t < W) p.srcflag[t] = 0ull;
     }
+    if (MODE == kModeScan && t < S) p.vsum[t] = 0.0;
     __syncthreads();
     if (t == 0) {
         p.lev_cnt[0] = (unsigned long long)s_valid;
@@ -201,7 +209,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
 #pragma unroll
         for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
         double sig[PL];
-        if (MODE == kModeSpd) {
+        if (MODE != kModeReach) {
 #pragma unroll
             for (int ii = 0; ii < PL; ++ii) sig[ii] = p.sigma[(size_t)v * S + lane + 32 * ii];
 #pragma unroll
@@ -218,7 +226,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
 #pragma unroll
             for (int w = 0; w < W; ++w)
                 if (lane == w) atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + w], (unsigned long long)F[w]);
-            if (MODE == kModeSpd) {
+            if (MODE != kModeReach) {
                 if (lane == 0) {
                     int pc = 0;
 #pragma unroll
@@ -258,7 +266,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     nm[w] = F[w] & ~(wrow[w] | wrow[cur * W + w]);
                     any |= nm[w] != 0ull;
                 }
-                if (MODE == kModeSpd) {
+                if (MODE != kModeReach) {
                     st.arcs += 1;
 #pragma unroll
                     for (int w = 0; w < W; ++w) st.tight += (unsigned)__popcll(nm[w]);
@@ -285,7 +293,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
                     wire = p.roff[wv + 1];
                 }
             }
-            if (MODE == kModeSpd) {
+            if (MODE != kModeReach) {
                 // two tight heads per step: their shuffles and atomics overlap
                 unsigned bal = __ballot_sync(kFull, any);
                 while (bal) {
@@ -321,7 +329,7 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
             if (app) {
                 wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
                 if (MODE == kModeSpd) winch = (int)((wire - wirb + CH - 1) / CH);
-                if (MODE == kModeSpd && old < 0) {
+                if (MODE != kModeReach && old < 0) {
                     st.vb += 1;
                     st.eb += (unsigned)(wre - wrb);
                 }
@@ -464,6 +472,107 @@ __device__ void level_outputs(const TravParams &p, int L, bool swap, bool set_ne
     }
 }
 
+// Dependencies on one query vertex r by a vertex scan, from the pair
+// dependencies of Eq. 2: r lies on sigma_sr * sigma_rt of the sigma_st
+// shortest s-t paths when d(s, r) + d(r, t) = d(s, t) (and on none
+// otherwise), so delta_s.(r) = sigma_sr * sum of sigma_rt / sigma_st over
+// those t != s, r. rlev and rsig hold d(r, t) and sigma_rt from a forward
+// traversal rooted at r. A level-L entry (t, F) lists the sources s with
+// d(s, t) = L, so source s takes t exactly when d(s, r) = L - d(r, t), and
+// every (t, s) pair is met once, in any order: there is no level order and
+// no barrier. Lanes first screen 32 entries at a time on d(r, t) against the
+// levels at which the tile's sources meet r; the survivors are taken two at
+// a time, each lane adding the terms of its sources l + 32 i in registers.
+// Each warp's sums, times sigma_sr, go to vsum with one fp64 atomic add per
+// source.
+template <int W>
+__device__ void vertex_scan(const TravParams &p, int Lmax, const uint64_t *s_need, long long gwarp,
+                            long long nwarps) {
+    constexpr int S = 64 * W;
+    constexpr int PL = 2 * W;
+    const int lane = threadIdx.x & 31;
+    int ks[PL];  // d(s, r) of the lane's sources, -1 for slots without a query
+    double a[PL];
+    int kmin = 0x7fffffff, kmax = -1;
+    uint64_t kset = 0ull;  // the levels below 64 at which some source meets r
+#pragma unroll
+    for (int ii = 0; ii < PL; ++ii) {
+        const int s = lane + 32 * ii;
+        const uint64_t x = s_need[s];
+        ks[ii] = x ? p.qlevel[s * 64 + __ffsll((long long)x) - 1] : -1;
+        a[ii] = 0.0;
+        if (ks[ii] >= 1) {
+            kmin = min(kmin, ks[ii]);
+            kmax = max(kmax, ks[ii]);
+            if (ks[ii] < 64) kset |= 1ull << ks[ii];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(kFull, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(kFull, kmax, o));
+        kset |= __shfl_xor_sync(kFull, kset, o);
+    }
+    unsigned pairs = 0;
+    if (kmax >= 1) {
+        for (int L = kmin + 1; L <= Lmax; ++L) {
+            const long long eend = p.lev_start[L + 1];
+            for (long long b = p.lev_start[L] + 32 * gwarp; b < eend; b += 32 * nwarps) {
+                const long long e = b + lane;
+                int t = 0, k = -1;
+                if (e < eend) {
+                    t = p.hv[e];
+                    const int dr = p.rlev[t];
+                    if (dr >= 1) k = L - dr;
+                }
+                const bool keep = k >= kmin && k <= kmax && (k >= 64 || ((kset >> k) & 1ull));
+                const double rs = keep ? p.rsig[t] : 0.0;
+                unsigned bal = __ballot_sync(kFull, keep);
+                while (bal) {
+                    const int i0 = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const int i1 = bal ? __ffs(bal) - 1 : -1;
+                    if (bal) bal &= bal - 1;
+                    const int j1 = i1 < 0 ? i0 : i1;
+                    const int t0 = __shfl_sync(kFull, t, i0);
+                    const int t1 = __shfl_sync(kFull, t, j1);
+                    const int k0 = __shfl_sync(kFull, k, i0);
+                    const int k1 = i1 < 0 ? -2 : __shfl_sync(kFull, k, j1);  // -2 matches no source
+                    const double r0 = __shfl_sync(kFull, rs, i0);
+                    const double r1 = __shfl_sync(kFull, rs, j1);
+                    uint64_t f0[W], f1[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        f0[w] = p.hm[(b + i0) * W + w];
+                        f1[w] = p.hm[(b + j1) * W + w];
+                    }
+                    const double *q0 = p.sigma + (size_t)t0 * S;
+                    const double *q1 = p.sigma + (size_t)t1 * S;
+#pragma unroll
+                    for (int ii = 0; ii < PL; ++ii) {
+                        const int s = lane + 32 * ii;
+                        if (ks[ii] == k0 && mask_bit<W>(f0, s)) {
+                            a[ii] += r0 / q0[s];
+                            ++pairs;
+                        }
+                        if (ks[ii] == k1 && mask_bit<W>(f1, s)) {
+                            a[ii] += r1 / q1[s];
+                            ++pairs;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    const double *sr = p.sigma + (size_t)p.vroot * S;
+#pragma unroll
+    for (int ii = 0; ii < PL; ++ii)
+        if (a[ii] != 0.0) atomicAdd(&p.vsum[lane + 32 * ii], sr[lane + 32 * ii] * a[ii]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+    if (lane == 0 && pairs) atomicAdd(&p.ctr->vpairs, (unsigned long long)pairs);
+}
+
 template <int W, int MODE, int MINB>
 __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
     constexpr int S = 64 * W;
@@ -489,7 +598,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         if (blockIdx.x == 0) init_tile<W, MODE>(p, tsrc);
         for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
-            s_need[s] = (MODE == kModeSpd && v >= 0) ? p.need[v] : 0ull;
+            s_need[s] = (MODE != kModeReach && v >= 0) ? p.need[v] : 0ull;
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
         if (timer) {
@@ -548,6 +657,21 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         }
 
         // ---------------- backward ----------------
+        if (MODE == kModeScan && (p.flags & kFlagRootOut)) {
+            // the query vertex's own traversal (source slot 0): keep d(r, t) and sigma_rt
+            for (int Lr = 0; Lr <= Lmax; ++Lr) {
+                const long long eend = p.lev_start[Lr + 1];
+                for (long long e = p.lev_start[Lr] + gthr; e < eend; e += nthr) {
+                    const int v = p.hv[e];
+                    p.rlev[v] = Lr;
+                    p.rsig[v] = p.sigma[(size_t)v * S];
+                }
+            }
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        } else if (MODE == kModeScan && !(p.flags & kFlagNoBackward)) {
+            vertex_scan<W>(p, Lmax, s_need, gwarp, nwarps);
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        }
         if (MODE == kModeSpd && !(p.flags & kFlagNoBackward)) {
             if (threadIdx.x == 0) s_lstop = 0x7fffffff;
             __syncthreads();
@@ -613,10 +737,23 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
             t_mark = t;
         }
 
-        if (MODE == kModeSpd) flush_stats(p.ctr, st, lane);
+        if (MODE != kModeReach) flush_stats(p.ctr, st, lane);
 
         // ---------------- tile end ----------------
-        if (MODE == kModeSpd && blockIdx.x == 0) tile_query_sums(p, tile, S, tsrc, s_need);
+        if (MODE == kModeScan && blockIdx.x == 0) {
+            // every query of a scan launch has the same vertex: one sum per source
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                uint64_t x = s_need[s];
+                const double d = p.vsum[s];
+                while (x) {
+                    const int q = __ffsll((long long)x) - 1;
+                    x &= x - 1;
+                    p.dep[s * 64 + q] = d;
+                }
+            }
+            __syncthreads();
+        }
+        if (MODE != kModeReach && blockIdx.x == 0) tile_query_sums(p, tile, S, tsrc, s_need);
         if (MODE == kModeReach) {
             for (long long e = gthr; e < total; e += nthr)
                 atomicOr((unsigned long long *)&p.rvmask[p.hv[e]], (unsigned long long)p.hm[e * W]);
@@ -624,7 +761,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         if (!(p.flags & kFlagNoReset)) {
             for (long long e = gwarp; e < total; e += nwarps) {
                 const int v = p.hv[e];
-                if (MODE == kModeSpd) {
+                if (MODE != kModeReach) {
                     uint64_t F[W];
 #pragma unroll
                     for (int w = 0; w < W; ++w) F[w] = p.hm[e * W + w];
@@ -635,7 +772,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                         const int s = lane + 32 * ii;
                         if (mask_bit<W>(F, s)) {
                             row[s] = 0.0;
-                            arow[s] = 0.0;
+                            if (MODE == kModeSpd) arow[s] = 0.0;
                         }
                     }
                 }
@@ -671,6 +808,7 @@ template <int W, int MODE, int MINB>
 bc_status launch(bc_graph *g, TravParams &p) {
     auto kern = trav_kernel<W, MODE, MINB>;
     const int threads = g->block_threads;
+    if (threads < 64 * W) return set_error(BC_E_INVALID_ARG, "block_threads must be at least 64 * tile_words");
     const size_t smem = 0;
     int per_sm = 0;
     BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -741,6 +879,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             if (W != 1) return set_error(BC_E_INTERNAL, "reach traversal runs with one mask word");
             st = launch<1, kModeReach, 2>(g, p);
         } else if (g->weighted) {
+            if (p.mode != kModeSpd) return set_error(BC_E_INTERNAL, "weighted traversals run the Eq. 4 backward only");
             p.wt = g->d_w;
             p.roff = g->d_roff;
             p.rcol = g->d_rcol;
@@ -756,6 +895,15 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             p.nw = W;
             p.lev_dist = ws.lev_dist;
             st = launch_weighted(g, p);
+        } else if (p.mode == kModeScan) {
+            if (W == 1)
+                st = launch<1, kModeScan, 2>(g, p);
+            else if (W == 2)
+                st = launch<2, kModeScan, 2>(g, p);
+            else if (W == 4)
+                st = g->blocks_per_sm == 2 ? launch<4, kModeScan, 2>(g, p) : launch<4, kModeScan, 1>(g, p);
+            else
+                return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
         } else if (W == 1) {
             st = launch<1, kModeSpd, 2>(g, p);
         } else if (W == 2) {

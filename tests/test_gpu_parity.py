@@ -30,9 +30,10 @@ def close(a, b, rel=REL):
 
 
 def make(bcd, g, **cfg):
+    """A graph handle on the Eq. 4 backward (the vertex scan, the default for
+    one-vertex calls, has its own tests)."""
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
-    if cfg:
-        bcd.bc_set_config(dg, **cfg)
+    bcd.bc_set_config(dg, **{"accumulation": 1, **cfg})
     return dg
 
 

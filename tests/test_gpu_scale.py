@@ -3,7 +3,8 @@
 
 R-MAT scale 20 (the exact batch): RV lists of all 64 queries bit-exact;
 dist and sigma of sampled union sources bit-exact and their dependencies on
-every query within 1e-9; full BC(r) for the queries the oracle can finish.
+every query within 1e-9; full BC(r) for the queries the oracle can finish;
+the vertex-scan accumulation on single queries.
 R-MAT scale 22 with 30 % reciprocal arcs (the sampled batch): the draws of
 eps = 0.01, delta = 0.1, seed 7 bit-exact, and the dependencies of drawn
 sources within 1e-9.
@@ -40,7 +41,7 @@ def rmat20(bcd):
     g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
     qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2)
+    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2, accumulation=1)
     return g, O.Graph.from_csr(g), dg, qs
 
 
@@ -87,11 +88,41 @@ def test_rmat20_small_queries_full(bcd, rmat20):
         assert o["rv_size"] == k and close(o["bc"], want), (r, o["bc"], want)
 
 
+def test_rmat20_vertex_scan(bcd, rmat20):
+    """accumulation = 2 at full size, one query per call: 96 draws on the top
+    in*out vertex (seed 7) against the oracle on the same draws; the bench's
+    14,979-draw query against the Eq. 4 path; the small exact queries against
+    the oracle."""
+    g, og, dg, qs = rmat20
+    top = qs[32]
+    want, _, k, _ = O.bc_approx(og, top, 96, 7, 0)
+    bcd.bc_set_config(dg, accumulation=2)
+    try:
+        out, info = bcd.bc_batch(dg, [{"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 96, "seed": 7}])
+        assert info["scan_pairs"] > 0 and out[0]["rv_size"] == k
+        assert close(out[0]["bc"], want), (out[0]["bc"], want)
+        big = {"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 14979, "seed": 7}
+        scan, _ = bcd.bc_batch(dg, [big])
+        small = []
+        for r in dict.fromkeys(qs):
+            kk = bcd.bc_rv_compute(dg, r).shape[0]
+            if 0 < kk <= 200:
+                small.append(r)
+        for r in small:
+            got, _ = bcd.bc_exact(dg, r)
+            assert close(got, O.bc_exact(og, r, 0)[0]), r
+    finally:
+        bcd.bc_set_config(dg, accumulation=1)
+    push, info = bcd.bc_batch(dg, [big])
+    assert info["scan_pairs"] == 0
+    assert close(scan[0]["bc"], push[0]["bc"]), (scan[0]["bc"], push[0]["bc"])
+
+
 @pytest.fixture(scope="module")
 def rmat22(bcd):
     g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2)
+    bcd.bc_set_config(dg, tile_words=4, chunk_arcs=128, blocks_per_sm=2, accumulation=1)
     return g, O.Graph.from_csr(g), dg
 
 
