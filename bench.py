@@ -467,15 +467,15 @@ def run_wprofile_case(args):
     """A small launch of the weighted traversal kernel for ncu captures: one
     sampled query (T = args.case_T draws, seed 7) on the vertex of largest
     in-degree x out-degree of R-MAT scale args.case_scale (edge factor 16,
-    seed 20) with weights uniform in [1, 255] (seed 3)."""
+    seed 20) with weights uniform in [1, 255] (seed 3); the Eq. 4 backward, or
+    the vertex scan with --accumulation 2."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1708_08739_gb300 as bcd
     g = gg.rmat(args.case_scale, 16, 0.57, 0.19, 0.19, seed=20)
     g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
-    if args.weighted_words:
-        bcd.bc_set_config(dg, weighted_words=args.weighted_words)
+    bcd.bc_set_config(dg, weighted_words=args.weighted_words, accumulation=args.accumulation or 1)
     r = int(gg.top_inout_vertices(g, 1)[0])
     out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
     print(json.dumps({"case": "wprofile", "scale": args.case_scale, "r": r, "T": args.case_T, "bc": out[0]["bc"],
@@ -608,7 +608,7 @@ def main():
                     help="single-query latency under both accumulations (Eq. 4 push, vertex scan)")
     ap.add_argument("--single-reps", type=int, default=5)
     ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2],
-                    help="profile case: 1 Eq. 4 backward (the case's default), 2 vertex scan")
+                    help="profile / wprofile cases: 1 Eq. 4 backward (their default), 2 vertex scan")
     ap.add_argument("--serve-queries", type=int, default=256)
     ap.add_argument("--serve-rv-max", type=int, default=100000)
     args = ap.parse_args()

@@ -311,10 +311,10 @@ void bc_server_destroy(bc_server *srv);
  *                  in half of the free device memory at about 40 bytes per
  *                  (vertex, source) pair. tile_words applies to unweighted
  *                  graphs only.
- *   accumulation   how the dependencies delta_s.(r) of a launch are summed
- *                  on unweighted graphs:
- *                  1 the backward pass of Eq. 4, pushed level by level
- *                  along the tight in-arcs of R(G);
+ *   accumulation   how the dependencies delta_s.(r) of a launch are summed:
+ *                  1 the backward pass of Eq. 4, deepest level first
+ *                  (unweighted: pushed along the tight in-arcs of R(G);
+ *                  weighted: pulled over the tight out-arcs);
  *                  2 (default) a vertex scan, used when every query of a
  *                  call (or of a bc_batch group) has the same vertex r,
  *                  else 1 (groups with several vertices, serving): one
@@ -326,9 +326,10 @@ void bc_server_destroy(bc_server *srv);
  *                  sigma_st(r) = sigma_sr * sigma_rt when r lies on a
  *                  shortest s-t path: the Bellman criterion),
  *                  one pass over the tile's reached (vertex, source) pairs
- *                  with no per-level barrier. Results equal those of 1 up
- *                  to fp64 rounding order. On the R-MAT graphs of the
- *                  benchmark a one-query call runs about 1.4x faster.
+ *                  with no per-level barrier, on unweighted and weighted
+ *                  graphs. Results equal those of 1 up to fp64 rounding
+ *                  order. On the R-MAT graphs of the benchmark a one-query
+ *                  call runs about 1.4x faster.
  * Zero fields keep their current value.
  */
 typedef struct {

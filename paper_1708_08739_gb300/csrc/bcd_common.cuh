@@ -129,9 +129,11 @@ struct TravParams {
     int32_t nw;              // 64-source words of a weighted tile (1, 2, 4, 8 or 16)
     int64_t *lev_dist;       // [maxlev + 2] distance of each non-empty level
     // vertex scan (one query vertex vroot): its forward traversal and per-source sums
-    int32_t *rlev;           // [n] d(vroot, t), -1 unreached
+    int32_t *rlev;           // [n] d(vroot, t), -1 unreached (unweighted)
+    uint64_t *rdist;         // [n] d(vroot, t), UINT64_MAX unreached (weighted)
     double *rsig;            // [n] sigma from vroot to t
-    double *vsum;            // [S] sigma_s(vroot) * sum_t sigma_rt / sigma_st of the current tile
+    double *vsum;            // [2 S] per-source sums of the current tile (unweighted: sigma_sr * sum_t
+                             // sigma_rt / sigma_st; weighted: sum_t sigma_rt / sigma_st, then sigma_sr)
     int32_t vroot;
     int32_t pad2;
     // reach mode output
@@ -194,8 +196,9 @@ struct bcd_workspace {
     int32_t *qlevel = nullptr;    // [64 * W * 64]
     double *dep = nullptr;        // [64 * W * 64]
     int32_t *rlev = nullptr;      // [n] vertex scan: levels from the query vertex (unweighted graphs)
+    uint64_t *rdist = nullptr;    // [n] ... distances from it (weighted graphs)
     double *rsig = nullptr;       // [n] ... and its path counts
-    double *vsum = nullptr;       // [64 * W] ... and the per-source sums of a tile
+    double *vsum = nullptr;       // [2 * 64 * W] ... and the per-source sums of a tile
     int32_t *rtile = nullptr;     // [64 * W] the one-source tile of the query vertex's traversal
     uint32_t *qflags = nullptr;   // [64]
     uint64_t *srcflag = nullptr;  // [W]

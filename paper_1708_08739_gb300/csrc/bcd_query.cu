@@ -310,6 +310,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.qlevel);
     dev_free(ws.dep);
     dev_free(ws.rlev);
+    dev_free(ws.rdist);
     dev_free(ws.rsig);
     dev_free(ws.vsum);
     dev_free(ws.rtile);
@@ -354,12 +355,14 @@ bc_status ensure_workspace(bc_graph *g, int W) {
     BCD_TRY(dev_alloc(&ws.dlist, (size_t)n + 64 * (size_t)W + 256));  // union padded to whole tiles
     BCD_TRY(dev_alloc(&ws.qlevel, (size_t)64 * W * 64));
     BCD_TRY(dev_alloc(&ws.dep, (size_t)64 * W * 64));
-    if (!g->weighted) {  // vertex scan state
+    // vertex scan state
+    if (g->weighted)
+        BCD_TRY(dev_alloc(&ws.rdist, (size_t)n));
+    else
         BCD_TRY(dev_alloc(&ws.rlev, (size_t)n));
-        BCD_TRY(dev_alloc(&ws.rsig, (size_t)n));
-        BCD_TRY(dev_alloc(&ws.vsum, (size_t)64 * W));
-        BCD_TRY(dev_alloc(&ws.rtile, (size_t)64 * W));
-    }
+    BCD_TRY(dev_alloc(&ws.rsig, (size_t)n));
+    BCD_TRY(dev_alloc(&ws.vsum, (size_t)2 * 64 * W));
+    BCD_TRY(dev_alloc(&ws.rtile, (size_t)64 * W));
     BCD_TRY(dev_alloc(&ws.qflags, 64));
     BCD_TRY(dev_alloc(&ws.srcflag, (size_t)std::max(W, 4)));
     BCD_TRY(dev_alloc(&ws.ctr, 1));
@@ -605,7 +608,10 @@ static bc_status root_traversal(bc_graph *g, int32_t r) {
     fill_i32<<<1, 256, 0, s>>>(ws.rtile, S, -1);
     fill_i32<<<1, 32, 0, s>>>(ws.rtile, 1, r);
     g->launches += 2;
-    BCD_CUDA(cudaMemsetAsync(ws.rlev, 0xff, sizeof(int32_t) * (size_t)g->n, s));
+    if (g->weighted)
+        BCD_CUDA(cudaMemsetAsync(ws.rdist, 0xff, sizeof(uint64_t) * (size_t)g->n, s));
+    else
+        BCD_CUDA(cudaMemsetAsync(ws.rlev, 0xff, sizeof(int32_t) * (size_t)g->n, s));
     BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, 64));
     TravParams p;
     memset(&p, 0, sizeof(p));
@@ -625,15 +631,14 @@ static bc_status root_traversal(bc_graph *g, int32_t r) {
     p.qflags = ws.qflags;
     p.srcflag = ws.srcflag;
     p.rlev = ws.rlev;
+    p.rdist = ws.rdist;
     p.rsig = ws.rsig;
     p.vsum = ws.vsum;
     p.vroot = r;
     return run_traversal(g, W, p, nullptr, nullptr);
 }
 
-static bool use_vertex_scan(const bc_graph *g, size_t nroots) {
-    return g->accumulation == 2 && !g->weighted && nroots == 1;
-}
+static bool use_vertex_scan(const bc_graph *g, size_t nroots) { return g->accumulation == 2 && nroots == 1; }
 
 static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm) {
     bcd_workspace &ws = g->ws;
@@ -759,6 +764,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         p.flags = 0;
         if (scan) {
             p.rlev = ws.rlev;
+            p.rdist = ws.rdist;
             p.rsig = ws.rsig;
             p.vsum = ws.vsum;
             p.vroot = roots[0];

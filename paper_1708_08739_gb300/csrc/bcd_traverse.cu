@@ -879,7 +879,6 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             if (W != 1) return set_error(BC_E_INTERNAL, "reach traversal runs with one mask word");
             st = launch<1, kModeReach, 2>(g, p);
         } else if (g->weighted) {
-            if (p.mode != kModeSpd) return set_error(BC_E_INTERNAL, "weighted traversals run the Eq. 4 backward only");
             p.wt = g->d_w;
             p.roff = g->d_roff;
             p.rcol = g->d_rcol;

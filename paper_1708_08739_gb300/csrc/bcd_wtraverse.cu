@@ -29,6 +29,13 @@
 // is summed by one lane in CSR order, a long row per lane in a fixed arc
 // order, then by a fixed butterfly per chunk, and the chunks are combined in
 // chunk order by the last one to finish, so delta is run-to-run reproducible.
+//
+// Scan mode (every query of the launch at one vertex r) replaces the backward
+// pass by one pass over the settled pairs: r lies on sigma_sr * sigma_rt of
+// the sigma_st shortest s-t paths when d(s, r) + d(r, t) = d(s, t), so
+// delta_s.(r) = sigma_sr * sum of sigma_rt / sigma_st over those t != s, r
+// (the pair dependencies of Eq. 2), with d(r, t) and sigma_rt from an earlier
+// scan-mode launch whose only source is r (kFlagRootOut).
 #include "bcd_common.cuh"
 #include "bcd_device.cuh"
 
@@ -254,6 +261,8 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             }
             for (int i = threadIdx.x; i < S * 64; i += blockDim.x) p.qlevel[i] = -1;
             for (int i = threadIdx.x; i < p.nw; i += blockDim.x) p.srcflag[i] = 0ull;
+            if (p.mode == kModeScan)
+                for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) p.vsum[i] = 0.0;
         }
         for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
@@ -413,8 +422,56 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             t_mark = t;
         }
 
+        // ---------------- the query vertex's own traversal ----------------
+        if (p.mode == kModeScan && (p.flags & kFlagRootOut)) {
+            // source slot 0 is r: keep d(r, t) and sigma_rt
+            for (long long e = gthr; e < total; e += nthr) {
+                const int v = p.hv[e];
+                const size_t iv = ((size_t)v << tl.shift) + p.hs[e];
+                p.rdist[v] = p.dist[iv];
+                p.rsig[v] = p.sigma[iv];
+            }
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        }
+        // ---------------- vertex scan over the settled pairs ----------------
+        // A settled pair (t, s) of level sg (distance D) takes the term
+        // sigma_rt / sigma_st when d(s, r) + d(r, t) = D, with d(r, t) >= 1
+        // (t != r). d(s, r) is the distance of the level at which r settled
+        // for s (its query level). Terms meet in vsum[s] by fp64 atomic adds;
+        // block 0 keeps sigma_sr in vsum[S + s] before the closing barrier.
+        if (p.mode == kModeScan && !(p.flags & (kFlagRootOut | kFlagNoBackward))) {
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                const uint64_t x = s_need[s];
+                const int qs = x ? p.qlevel[s * 64 + __ffsll((long long)x) - 1] : -1;
+                s_minql[s] = qs;
+                if (blockIdx.x == 0) p.vsum[S + s] = qs >= 0 ? p.sigma[((size_t)p.vroot << tl.shift) + s] : 0.0;
+            }
+            __syncthreads();
+            unsigned pairs = 0;
+            for (int sg = 1; sg < nseg; ++sg) {
+                const long long e0 = p.lev_start[sg];
+                const long long ne = (long long)p.lev_cnt[sg];
+                const unsigned long long dk = (unsigned long long)p.lev_dist[sg];
+                for (long long i = gthr; i < ne; i += nthr) {
+                    const long long e = e0 + i;
+                    const int v = p.hv[e];
+                    const unsigned long long rd = p.rdist[v];
+                    if (rd == 0ull || rd >= dk) continue;  // t = r, t unreached from r, or d(s, r) < 1
+                    const int s = p.hs[e];
+                    const int qs = s_minql[s];
+                    if (qs < 0 || (unsigned long long)p.lev_dist[qs] + rd != dk) continue;
+                    atomicAdd(&p.vsum[s], p.rsig[v] / p.sigma[((size_t)v << tl.shift) + s]);
+                    ++pairs;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+            if (lane == 0 && pairs) atomicAdd(&p.ctr->vpairs, (unsigned long long)pairs);
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        }
+
         // ---------------- backward (Eq. 4) over the levels ----------------
-        if (!(p.flags & kFlagNoBackward)) {
+        if (p.mode == kModeSpd && !(p.flags & kFlagNoBackward)) {
             if (threadIdx.x == 0) s_lstop = 0x7fffffff;
             __syncthreads();
             for (int s = threadIdx.x; s < S; s += blockDim.x) {
@@ -508,6 +565,19 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
         wflush(p.ctr, st, lane);
 
         // ---------------- tile end ----------------
+        if (p.mode == kModeScan && blockIdx.x == 0) {
+            // every query of a scan launch has the same vertex: one value per source
+            for (int s = threadIdx.x; s < S; s += blockDim.x) {
+                uint64_t x = s_need[s];
+                const double dv = p.vsum[S + s] * p.vsum[s];
+                while (x) {
+                    const int q = __ffsll((long long)x) - 1;
+                    x &= x - 1;
+                    p.dep[s * 64 + q] = dv;
+                }
+            }
+            __syncthreads();
+        }
         if (blockIdx.x == 0) tile_query_sums(p, tile, S, tsrc, s_need);
         if (!(p.flags & kFlagNoReset)) {
             for (long long e = gthr; e < total; e += nthr) {

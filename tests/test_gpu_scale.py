@@ -11,8 +11,8 @@ sources within 1e-9.
 The R-MAT scale 20 graph with weights uniform in [1, 255] (seed 3; the
 weighted batch of 32 uniform queries, seed 104), in the default weighted tile
 width: RV lists bit-exact, uint64 distances and sigma of sampled sources
-bit-exact and their dependencies on all 32 queries within 1e-9, and the
-queries with empty RV answered 0.
+bit-exact and their dependencies on all 32 queries within 1e-9, the
+queries with empty RV answered 0, and the vertex scan on a sampled query.
 """
 import numpy as np
 import pytest
@@ -160,6 +160,7 @@ def rmat20w(bcd):
     g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     qs = [int(x) for x in gg.random_vertices(g.n, 32, 104)]
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    bcd.bc_set_config(dg, accumulation=1)
     return g, O.Graph.from_csr(g), dg, qs
 
 
@@ -188,6 +189,29 @@ def test_rmat20_weighted_sampled_sources(bcd, rmat20w):
         for j in range(qv.shape[0]):
             if qv[j] != s:
                 assert close(dep[i, j], odep[i, j]), (s, int(qv[j]), dep[i, j], odep[i, j])
+
+
+def test_rmat20_weighted_vertex_scan(bcd, rmat20w):
+    """accumulation = 2 on the weighted graph at full size: 48 draws (seed 7)
+    on the vertex of largest in*out degree, against the oracle on the same
+    draws and against the Eq. 4 path."""
+    g, og, dg, qs = rmat20w
+    # the vertex of largest in*out degree: RV is the giant component and the
+    # score is far from 0 (the giant-component queries of the batch have one
+    # out-arc or none, and 48 draws give them 0)
+    top = int(gg.top_inout_vertices(g, 1)[0])
+    spec = {"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 48, "seed": 7}
+    want = O.bc_approx(og, top, 48, 7, 0)[0]
+    assert want > 0.0
+    push, info = bcd.bc_batch(dg, [spec])
+    assert info["scan_pairs"] == 0
+    bcd.bc_set_config(dg, accumulation=2)
+    try:
+        scan, info = bcd.bc_batch(dg, [spec])
+    finally:
+        bcd.bc_set_config(dg, accumulation=1)
+    assert info["scan_pairs"] > 0
+    assert close(scan[0]["bc"], want) and close(push[0]["bc"], want), (scan[0]["bc"], push[0]["bc"], want)
 
 
 def test_rmat20_weighted_empty_rv_queries(bcd, rmat20w):

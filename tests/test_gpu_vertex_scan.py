@@ -8,7 +8,9 @@ the same pair dependencies (Eq. 2) in another grouping, so the bar is a
 relative 1e-9, and equality where every term is an integer. Sizes span
 several tiles with ragged tails; the edge cases are the ones of the Eq. 4
 path (trivial zero, empty RV, long level chains, split rows, sigma past
-2^53). Calls whose queries sit at more than one vertex keep the Eq. 4 path.
+2^53). Unweighted graphs scan the per-level (vertex, source mask) entries,
+weighted graphs the settled (vertex, source) pairs. Calls whose queries sit
+at more than one vertex keep the Eq. 4 path.
 """
 import numpy as np
 import pytest
@@ -161,14 +163,81 @@ def test_scan_mixed_vertices_keep_eq4(bcd, er1):
         assert close(o["bc"], O.bc_exact(og, r, 0)[0])
 
 
-def test_scan_weighted_graph_keeps_eq4(bcd):
-    g = gg.erdos_renyi(300, 1500, 21)
-    g = g.with_weights(gg.uniform_weights(g.m, 1, 3, 4))
+@pytest.fixture(scope="module")
+def wer():
+    """ER 600 / 4,000 with weights uniform in [1, 255] (seed 3) and in [1, 3]
+    (seed 4: many equal-length paths, sigma > 1)."""
+    g = gg.erdos_renyi(600, 4000, 21)
+    g255 = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    g3 = g.with_weights(gg.uniform_weights(g.m, 1, 3, 4))
+    return [(x, O.Graph.from_csr(x)) for x in (g255, g3)]
+
+
+@pytest.mark.parametrize("cfg", [{}, {"weighted_words": 1}, {"weighted_words": 16, "chunk_arcs": 32}])
+@pytest.mark.parametrize("which", [0, 1])
+def test_scan_weighted_matches_oracle(bcd, wer, which, cfg):
+    """Weighted graphs: the scan over settled (vertex, source) pairs, exact
+    and sampled, in 64-, 256- and 1024-source tiles."""
+    g, og = wer[which]
+    dg = make(bcd, g, **cfg)
+    for r in gg.random_vertices(g.n, 10, 104).tolist():
+        o, info = scan_one(bcd, dg, {"r": r})
+        want, k, _ = O.bc_exact(og, r, 0)
+        assert o["rv_size"] == k and close(o["bc"], want), (r, o["bc"], want)
+        if want > 0.0:
+            assert info["scan_pairs"] > 0 and info["ms_root"] > 0.0, info
+    for r, T, seed in [(4, 600, 7), (77, 300, 9)]:
+        want = O.bc_approx(og, r, T, seed, 0)[0]
+        o, _ = scan_one(bcd, dg, {"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": T, "seed": seed})
+        assert close(o["bc"], want), (r, o["bc"], want)
+
+
+def test_scan_weighted_closed_forms(bcd):
+    # a->b (2), a->c (1), c->b (1): two shortest a-b paths, one through c
+    dg = make(bcd, csr(3, [(0, 1), (0, 2), (2, 1)], [2, 1, 1]))
+    assert bcd.bc_exact(dg, 2)[0] == 0.5
+    # weighted path: only the hop structure matters
+    dg = make(bcd, csr(5, [(i, i + 1) for i in range(4)], [7, 1, 255, 3]))
+    assert [bcd.bc_exact(dg, r)[0] for r in range(5)] == [0.0, 3.0, 4.0, 3.0, 0.0]
+
+
+def test_scan_weighted_repeated_multitile(bcd, wer):
+    """Ten 64-source tiles per launch (weights 1..3), repeated with several
+    block sizes."""
+    g, og = wer[1]
+    qs = gg.random_vertices(g.n, 4, 104).tolist()
+    want = {r: O.bc_exact(og, r, 0)[0] for r in qs}
+    for it in range(4):
+        dg = make(bcd, g, weighted_words=1, block_threads=(512, 256, 128, 384)[it])
+        for r in qs:
+            got = bcd.bc_exact(dg, r)[0]
+            assert close(got, want[r]), (it, r, got, want[r])
+        dg.close()
+
+
+def test_scan_weighted_rmat_small(bcd):
+    """Weighted R-MAT scale 12 (weights 1..255): hub rows split into chunks;
+    scan and Eq. 4 against the oracle."""
+    g = gg.rmat(12, 8, seed=12)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     og = O.Graph.from_csr(g)
+    scan = make(bcd, g)
+    push = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    bcd.bc_set_config(push, accumulation=1)
+    for r in gg.top_inout_vertices(g, 2).tolist() + gg.random_vertices(g.n, 4, 104).tolist():
+        want = O.bc_exact(og, r, 0)[0]
+        a = bcd.bc_exact(scan, r)[0]
+        b = bcd.bc_exact(push, r)[0]
+        assert close(a, want) and close(b, want), (r, a, b, want)
+
+
+def test_scan_weighted_mixed_vertices_keep_eq4(bcd, wer):
+    g, og = wer[0]
     dg = make(bcd, g)
-    o, info = scan_one(bcd, dg, {"r": 17})
-    assert info["scan_pairs"] == 0
-    assert close(o["bc"], O.bc_exact(og, 17, 0)[0])
+    out, info = bcd.bc_batch(dg, [{"r": 5}, {"r": 9}])
+    assert info["scan_pairs"] == 0 and info["ms_root"] == 0.0
+    for r, o in zip((5, 9), out):
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0])
 
 
 def test_scan_closed_forms(bcd):
