@@ -92,6 +92,37 @@ def bfs_dist_sigma(g, s):
     return dist, sig
 
 
+def dijkstra_dist_sigma(g, s):
+    """Weighted shortest paths from s: distances (-1 unreached) by Dijkstra
+    with a binary heap, then exact sigma by visiting vertices in increasing
+    distance (weights are positive, so a tight arc climbs in distance)."""
+    import heapq
+    n = g.n
+    w = g.weights
+    dist = [-1] * n
+    best = {s: 0}
+    pq = [(0, s)]
+    while pq:
+        d, x = heapq.heappop(pq)
+        if dist[x] >= 0:
+            continue
+        dist[x] = d
+        for e in range(g.offsets[x], g.offsets[x + 1]):
+            y = int(g.cols[e])
+            nd = d + int(w[e])
+            if dist[y] < 0 and nd < best.get(y, nd + 1):
+                best[y] = nd
+                heapq.heappush(pq, (nd, y))
+    sig = [0] * n
+    sig[s] = 1
+    for x in sorted((v for v in range(n) if dist[v] >= 0), key=lambda v: dist[v]):
+        for e in range(g.offsets[x], g.offsets[x + 1]):
+            y = int(g.cols[e])
+            if dist[y] == dist[x] + int(w[e]):
+                sig[y] += sig[x]
+    return dist, sig
+
+
 def random_digraph(n, p, seed, weighted=False, wmax=4):
     r = np.random.default_rng(seed)
     arcs = [(u, v) for u in range(n) for v in range(n) if u != v and r.random() < p]

@@ -10,7 +10,9 @@ index, or a transposed operand fails at least one of them:
 * Section 2 (d, sigma): scipy BFS/Dijkstra distances; closed-form path counts
   (diamond chain sigma = 2^k, grid DAG sigma = binomial).
 * Eq. 4 (recursion): closed forms on paths, cycles, stars, diamonds; an
-  independent dependency formula from two BFS runs; the global sum identity.
+  independent dependency formula (pair dependencies of Eq. 2) from two BFS
+  runs, and from two Dijkstra runs on weighted graphs; the global sum
+  identity.
 * Prop. 1 / Eq. 5 (pruning), Prop. 2 (RV via R(G)): all-sources equality and
   forward reachability through scipy.
 * Algorithm 2 / Props. 3-4: Philox against numpy's Philox, unbiasedness over
@@ -25,7 +27,7 @@ import pytest
 
 import graphgen as gg
 import oracle as O
-from helpers import arcs_of, bfs_dist_sigma, brute_force_bc, csr, random_digraph
+from helpers import arcs_of, bfs_dist_sigma, brute_force_bc, csr, dijkstra_dist_sigma, random_digraph
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
 
@@ -267,6 +269,30 @@ def test_dependency_matches_pair_formula():
                 if ds[r] + dr[t] == ds[t]:
                     tot += Fraction(ss[r] * sr[t], ss[t])
             assert dep[i, 0] == pytest.approx(float(tot), rel=1e-12, abs=1e-12)
+
+
+def test_weighted_dependency_matches_pair_formula():
+    """The same identity with weighted distances (weights 1..3: many ties, so
+    sigma > 1): Eq. 4 in the oracle against the pair dependencies of Eq. 2
+    from two Dijkstra runs, the formula the weighted vertex scan sums."""
+    g = gg.erdos_renyi(100, 400, 29).with_weights(gg.uniform_weights(400, 1, 3, 5))
+    G = og(g)
+    checked = 0
+    for r in [2, 40, 77]:
+        dr, sr = dijkstra_dist_sigma(g, r)
+        srcs = O.rv(G, r)[:20]
+        dep, _, _ = O.dependencies(G, srcs, [r], nthreads=2)
+        for i, s in enumerate(srcs.tolist()):
+            ds, ss = dijkstra_dist_sigma(g, s)
+            tot = Fraction(0)
+            for t in range(g.n):
+                if t in (s, r) or ds[t] < 0 or dr[t] < 0:
+                    continue
+                if ds[r] + dr[t] == ds[t]:
+                    tot += Fraction(ss[r] * sr[t], ss[t])
+            assert dep[i, 0] == pytest.approx(float(tot), rel=1e-12, abs=1e-12)
+            checked += tot > 0
+    assert checked > 5
 
 
 def test_sum_identity_unweighted():
