@@ -1,16 +1,22 @@
-"""Benchmark: batched exact BC(r) on a directed R-MAT scale-20 graph.
+"""Benchmark: batched sampled BC(r) on a directed R-MAT scale-22 graph.
 
-Workload (one step): one bc_batch call of 64 exact queries (32 uniform random
-vertices and the 32 vertices of largest in-degree x out-degree) on R-MAT
-scale 20, edge factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, self-loops and
-repeated arcs removed, unweighted. The metric is BC(r) queries per second;
-GTEPS (sum over sources of the arcs they reach, per second) is reported too.
+Workload (one step): one batch of 64 A-BCD queries (Algorithm 2; eps 0.01,
+delta 0.1, so T = 14,979 draws each, Philox seed 7) at 64 uniform random
+vertices (seed 105) of R-MAT scale 22, edge factor 8, a/b/c/d =
+0.57/0.19/0.19/0.05 (seed 22), with 30 % of the arcs also added reversed
+(seed 22), self-loops and repeated arcs removed, unweighted. The metric is
+BC(r) queries per second; GTEPS (sum over sources of the arcs they reach, per
+second) is reported too. At one GPU the line also carries the exact batch of
+64 queries on R-MAT scale 20 (edge factor 16) and a short serving run
+(continuous batching with Poisson arrivals, p50/p99 latency).
 
 Arms:
-  default            the CUDA library (libbcd.so) on one GPU per rank; under
-                     torchrun every rank solves its own copy of the batch
-                     (independent problems, weak scaling, no collective on
-                     the data path; the step time is the max over ranks).
+  default            the CUDA library (libbcd.so). Under torchrun the ranks
+                     share the one batch: rank k runs shard k of the batch's
+                     source tiles (bc_batch_shard) on its own replica of the
+                     graph, and the per-query partial scores are exchanged
+                     and summed in shard order (strong scaling: the total
+                     work is fixed as N grows).
   --impl reference   the CPU oracle as it stands, on the host cores, on a
                      bounded sample of the same batch's sources.
 
@@ -19,8 +25,8 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -34,18 +40,28 @@ sys.path.insert(0, ROOT)
 import graphgen as gg  # noqa: E402
 
 METRIC = "GTEPS and BC(r) queries/s (exact and sampled) vs HBM roofline; p50/p99 query latency"
-WORKLOAD = "rmat20_ef16_exact64"
-# dram bytes per (source x reached arc) of the traversal kernel, per workload,
-# from one-pass ncu captures of each workload's full launch, summarised in
-# profiles/trav_kernel_rmat20_exact64_w4.md and
-# profiles/trav_kernel_rmat22_recip30_sampled64_w4.md (256-source tiles); a
-# workload without an entry, another tile width, or a kernel changed since the
-# capture, reports traffic null
-TRAFFIC_BYTES_PER_EDGE = {"rmat20_ef16_exact64": 9.42, "rmat22_ef8_recip30_sampled64": 12.33}
+WORKLOAD = "rmat22_ef8_recip30_sampled64"
+
+# DRAM bytes per (source, reached arc) of the batched traversal kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch over the edges it
+# traversed), measured with ncu on a small launch of the same kernel (one
+# sampled query, 512 draws, on the R-MAT scale 20 graph: --case profile) and
+# scaled to the bench's launch by its edge count. The figure belongs to the
+# kernel sources it was taken on: when their hash differs, traffic is null.
+KERNEL_SOURCES = ["bcd_traverse.cu", "bcd_device.cuh", "bcd_common.cuh"]
+TRAFFIC = {"sources_sha256": None, "bytes_per_reached_arc": None, "tile_words": 4}
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1708_08739_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 WORKLOADS = {
@@ -137,10 +153,13 @@ def oracle_union(g, qs, specs=None):
     og = O.Graph.from_csr(g)
     union = set()
     outd = g.out_degree()
+    rv_cache = {}
     for i, r in enumerate(qs):
         if outd[r] == 0:
             continue
-        rvl = O.rv(og, r)
+        if r not in rv_cache:
+            rv_cache[r] = O.rv(og, r)
+        rvl = rv_cache[r]
         spec = specs[i] if specs else {"r": r}
         if spec.get("kind", 0) == 0:
             union.update(rvl.tolist())
@@ -151,16 +170,22 @@ def oracle_union(g, qs, specs=None):
     return og, np.array(sorted(union), dtype=np.int32)
 
 
-def oracle_sample(og, D, qs, n_sources, threads, seed=7):
-    """Times the oracle on a sample of the batch's sources: delta_s.(r_q) for
-    every query q and sampled source s. Returns (seconds, sources timed)."""
+def oracle_timed(og, D, qs, threads, budget_s, seed=7, chunk=None):
+    """Times the oracle on sources of the batch drawn at random from D:
+    delta_s.(r_q) for every query q, in chunks of `chunk` sources (default:
+    one per thread) until budget_s seconds have passed. Returns (seconds,
+    sources timed)."""
     import oracle as O
     rng = np.random.default_rng(seed)
-    pick = np.sort(rng.choice(D.shape[0], size=min(n_sources, D.shape[0]), replace=False))
-    srcs = D[pick]
-    t = time.time()
-    O.dependencies(og, srcs, np.array(qs, dtype=np.int32), nthreads=threads)
-    return time.time() - t, int(srcs.shape[0])
+    order = rng.permutation(D.shape[0])
+    chunk = chunk or threads
+    qv = np.array(qs, dtype=np.int32)
+    done, t0 = 0, time.time()
+    while done < D.shape[0] and (time.time() - t0 < budget_s or done == 0):
+        srcs = np.sort(D[order[done:done + chunk]])
+        O.dependencies(og, srcs, qv, nthreads=threads)
+        done += srcs.shape[0]
+    return time.time() - t0, done
 
 
 def max_over_ranks(value, dist=None, device="cuda"):
@@ -174,9 +199,19 @@ def max_over_ranks(value, dist=None, device="cuda"):
     return float(t.item())
 
 
-def job_rate(units_per_rank, ms, world):
-    """Whole-job throughput: units of all ranks per second of the slowest."""
-    return world * units_per_rank / (ms / 1000.0)
+def sum_over_ranks(value, dist=None, device="cuda"):
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units, ms):
+    """Whole-job throughput: the job's units (each query of the shared batch
+    once) per second of the slowest rank."""
+    return units / (ms / 1000.0)
 
 
 def run_reference(args):
@@ -187,25 +222,55 @@ def run_reference(args):
     ob.build()
     g, qs, specs = make_workload(args.workload)
     threads = os.cpu_count() or 1
-    per_step = 64
     og, D = oracle_union(g, qs, specs)
     nd = int(D.shape[0])
     times = []
+    per_step = []
     for i in range(args.warmup + args.steps):
-        el, ns = oracle_sample(og, D, qs, per_step, threads, seed=i)
+        el, ns = oracle_timed(og, D, qs, threads, args.ref_step_s, seed=i)
         if i >= args.warmup:
             times.append(el / ns)
+            per_step.append(ns)
     t_src = sum(times) / len(times)
     qps = len(qs) / (t_src * nd)
     line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(qs) / qps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "queries": len(qs), "sources_in_union": nd},
             "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
-                             "sample": "%d of the %d union sources per step, all 64 queries; queries/s = 64 / "
-                                       "(seconds per source x union size)" % (per_step, nd)},
+                             "sample": "per step, random union sources in chunks of %d until %.0f s (%d..%d "
+                                       "sources), delta for all %d queries; queries/s = %d / (seconds per source "
+                                       "x union size %d)" % (threads, args.ref_step_s, min(per_step),
+                                                             max(per_step), len(qs), len(qs), nd)},
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def solve_step(bcd, dg, specs, rank, world, dist):
+    """One step: this rank's shard of the batch, then the exchange of the
+    per-query partial scores (summed in shard order). Returns (scores, info
+    of this rank's launch, results of this rank)."""
+    from paper_1708_08739_gb300 import shard as sh
+    if world == 1:
+        out, info = bcd.bc_batch(dg, specs)
+        return np.array([o["bc"] for o in out]), info, out
+    box = {}
+
+    def solve(k):
+        out, info = bcd.bc_batch_shard(dg, specs, k, world)
+        box["info"], box["out"] = info, out
+        return [o["bc"] for o in out]
+
+    tot = sh.run_sharded(solve, world, rank, range(world), len(specs), dist)
+    return tot, box["info"], box["out"]
+
+
+def algorithmic_bytes(info):
+    """The kernel's algorithmic bytes for a launch (see the design notes):
+    graph structure 2 (8 |V_B| + 4 |E_B|) summed over tiles, 40 bytes per
+    reached (source, vertex) pair and 24 per tight (source, arc) pair."""
+    return (2.0 * (8.0 * info["union_vertices"] + 4.0 * info["union_arcs"]) + 40.0 * info["reached_pairs"] +
+            24.0 * info["tight_pairs"])
 
 
 def run_gpu(args):
@@ -225,17 +290,18 @@ def run_gpu(args):
     g, qs, specs = make_workload(args.workload)
     log("workload built in %.1fs: n=%d m=%d" % (time.time() - t0, g.n, g.m))
     # the oracle's CPU baseline runs on the host cores meanwhile (one core is
-    # left to the thread that drives the GPU)
+    # left to the thread that drives the GPU), on rank 0 at N = 1 only
     cpu_box = {}
     cpu_thread = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import threading
 
         def cpu_job():
             threads = max(1, (os.cpu_count() or 2) - 1)
             og, D = oracle_union(g, qs, specs)
-            el, ns = oracle_sample(og, D, qs, args.cpu_sources, threads)
-            cpu_box.update(el=el, ns=ns, nd=int(D.shape[0]), threads=threads)
+            el, ns = oracle_timed(og, D, qs, threads, args.cpu_budget_s)
+            el1, ns1 = oracle_timed(og, D, qs, 1, args.cpu_budget_s / 3.0, seed=8, chunk=1)
+            cpu_box.update(el=el, ns=ns, el1=el1, ns1=ns1, nd=int(D.shape[0]), threads=threads)
 
         cpu_thread = threading.Thread(target=cpu_job, daemon=True)
         cpu_thread.start()
@@ -250,7 +316,7 @@ def run_gpu(args):
 
     for i in range(args.warmup):
         t = time.time()
-        out, info = bcd.bc_batch(dg, specs)
+        solve_step(bcd, dg, specs, rank, world, dist)
         log("warmup %d: %.2fs" % (i, time.time() - t))
     clocks = ClockSampler(local)
     barrier()
@@ -260,27 +326,25 @@ def run_gpu(args):
     ev0.record(stream)
     infos = []
     for i in range(args.steps):
-        out, info = bcd.bc_batch(dg, specs)
+        scores, info, out = solve_step(bcd, dg, specs, rank, world, dist)
         infos.append(info)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist if world > 1 else None)
     nq = len(qs)
-    qps = job_rate(nq, ms, world)
+    qps = job_rate(nq, ms)
     edges = float(np.mean([i["edges_traversed"] for i in infos]))
-    gteps = world * edges / (ms / 1000.0) / 1e9
+    gteps = sum_over_ranks(edges, dist if world > 1 else None) / (ms / 1000.0) / 1e9
     trav_ms = float(np.mean([i["ms_traversal"] for i in infos]))
-    reached = float(np.mean([i["reached_pairs"] for i in infos]))
-    tight = float(np.mean([i["tight_pairs"] for i in infos]))
-    vb = float(np.mean([i["union_vertices"] for i in infos]))
-    eb = float(np.mean([i["union_arcs"] for i in infos]))
     launches = int(sum(i["launches"] for i in infos) / args.steps)
-    algo_bytes = 2.0 * (8.0 * vb + 4.0 * eb) + 40.0 * reached + 24.0 * tight
+    algo_bytes = float(np.mean([algorithmic_bytes(i) for i in infos]))
     peak, peak_kind = peaks()
     achieved = algo_bytes / (trav_ms / 1000.0) / 1e9
-    tb = TRAFFIC_BYTES_PER_EDGE.get(args.workload) if args.tile_words == 4 else None
-    traffic = None if tb is None else tb * edges
+    traffic = None
+    if (TRAFFIC["bytes_per_reached_arc"] and TRAFFIC["sources_sha256"] == kernel_sha() and
+            args.tile_words == TRAFFIC["tile_words"]):
+        traffic = TRAFFIC["bytes_per_reached_arc"] * edges
 
     # end to end through the C ABI: pinned host CSR in, results out
     off_h = torch.from_numpy(g.offsets).pin_memory()
@@ -289,31 +353,40 @@ def run_gpu(args):
     t = time.time()
     ge = bcd.bc_graph_create(g.n, off_h.numpy(), col_h.numpy(), stream=stream.cuda_stream)
     bcd.bc_set_config(ge, tile_words=args.tile_words)
-    out_e, info_e = bcd.bc_batch(ge, specs)
+    scores_e, _, _ = solve_step(bcd, ge, specs, rank, world, dist)
     ge.close()
     barrier()
     e2e_s = max_over_ranks(time.time() - t, dist if world > 1 else None)
     h2d = g.offsets.nbytes + g.cols.nbytes + nq * 40
     d2h = nq * 32
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras = run_extras(args, bcd, dg, g, stream)
     cpu = None
     if cpu_thread is not None:
         cpu_thread.join()
         t_src = cpu_box["el"] / cpu_box["ns"]
+        t_src1 = cpu_box["el1"] / cpu_box["ns1"]
         nd = cpu_box["nd"]
         cpu = {"value": nq / (t_src * nd), "unit": "queries/s", "cores": cpu_box["threads"], "kind": "oracle",
-               "sample": "%d of the %d union sources, delta for all 64 queries; queries/s = 64 / "
-                         "(seconds per source x union size)" % (cpu_box["ns"], nd)}
+               "sample": "%d random sources of the %d in the batch's union (chunks of one source per thread for "
+                         "%.0f s), delta for all %d queries; queries/s = %d / (seconds per source x union size)"
+                         % (cpu_box["ns"], nd, args.cpu_budget_s, nq, nq),
+               "single_thread": {"value": nq / (t_src1 * nd), "unit": "queries/s", "cores": 1,
+                                 "sample": "%d sources one at a time" % cpu_box["ns1"]}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
             "config": {"workload": args.workload, "recipe": WORKLOADS[args.workload],
                        "n": g.n, "m": g.m, "queries": nq,
-                       "tile_words": args.tile_words, "sources_in_union": int(infos[-1]["sources_run"]),
-                       "l2": "not flushed: working set (sigma slab, graph, level history) well above L2",
-                       "parallelism": "replicas: each rank solves its own batch"},
+                       "tile_words": args.tile_words, "sources_in_union": int(infos[-1]["sources_run"]) * world,
+                       "l2": "not flushed: working set (sigma and accumulator slabs, graph, level history) well above L2",
+                       "parallelism": "sources sharded: rank k runs shard k of each group's tiles, per-query "
+                                      "partials summed in shard order" if world > 1 else "one GPU"},
             "gteps": gteps,
             "phases_ms": {"rv": float(np.mean([i["ms_rv"] for i in infos])),
                           "sample": float(np.mean([i["ms_sample"] for i in infos])),
@@ -324,18 +397,64 @@ def run_gpu(args):
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": "trav_kernel (batched SPD + dependency traversal)",
                          "algorithmic_bytes": algo_bytes},
-            "e2e": {"value": job_rate(nq, 1000.0 * e2e_s, world), "unit": "queries/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(nq, 1000.0 * e2e_s), "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
-            "check": {"bc_first": out[0]["bc"], "e2e_equal": all(abs(a["bc"] - b["bc"]) <= 1e-9 * max(1, abs(b["bc"]))
-                                                                  for a, b in zip(out_e, out))},
+            "check": {"bc_first": float(scores[0]),
+                      "e2e_equal": all(abs(a - b) <= 1e-9 * abs(b) or a == b == 0.0 for a, b in zip(scores_e, scores))},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     dg.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_extras(args, bcd, dg22, g22, stream):
+    """Extra keys of the one-GPU line: the exact R-MAT 20 batch (one warm
+    and one timed call) and a short serving run on the resident R-MAT 22
+    graph."""
+    import torch
+    out = {}
+    g, qs, specs = make_workload("rmat20_ef16_exact64")
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, stream=stream.cuda_stream)
+    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    bcd.bc_batch(dg, specs)
+    torch.cuda.synchronize()
+    t = time.time()
+    res, info = bcd.bc_batch(dg, specs)
+    wall = time.time() - t
+    ab = algorithmic_bytes(info)
+    peak, _ = peaks()
+    out["rmat20_ef16_exact64"] = {
+        "recipe": WORKLOADS["rmat20_ef16_exact64"], "queries_per_s": len(qs) / wall, "s_per_batch": wall,
+        "gteps": info["edges_traversed"] / wall / 1e9, "sources_in_union": info["sources_run"],
+        "ms_traversal": info["ms_traversal"], "algorithmic_gbs": ab / (info["ms_traversal"] / 1000.0) / 1e9,
+        "frac": ab / (info["ms_traversal"] / 1000.0) / 1e9 / peak, "bc_first": res[0]["bc"]}
+    dg.close()
+    if args.serve_extra > 0:
+        specs_s, draws, rvs = serve_workload(bcd, dg22, g22, args.serve_extra, args.serve_rv_max)
+        srv = bcd.Server(dg22)
+        serve_run(bcd, srv, specs_s[: max(4, len(specs_s) // 8)])  # warm-up
+        wall, lat = serve_run(bcd, srv, specs_s)
+        sat = len(specs_s) / wall
+        w2, l2 = serve_run(bcd, srv, specs_s, rate=0.8 * sat, seed=80)
+        srv.close()
+        t = time.time()
+        for s in specs_s[:32]:
+            bcd.bc_batch(dg22, [s])
+        one = 32 / (time.time() - t)
+        out["serving"] = {
+            "workload": "R-MAT 22 + 30% reciprocal resident; %d Zipf(1.1) queries alternating exact (|RV| <= %d) "
+                        "and sampled (eps 0.02, delta 0.1, seed 7)" % (len(specs_s), args.serve_rv_max),
+            "closed_loop": {"queries_per_s": sat, "p50_ms": float(np.percentile(lat, 50)),
+                            "p99_ms": float(np.percentile(lat, 99))},
+            "poisson_0.8x": {"arrival_rate": 0.8 * sat, "queries_per_s": len(specs_s) / w2,
+                             "p50_ms": float(np.percentile(l2, 50)), "p99_ms": float(np.percentile(l2, 99))},
+            "one_at_a_time_queries_per_s": one}
+    return out
 
 
 def serve_workload(bcd, dg, g, nq, rv_max, seed=106):
@@ -453,7 +572,7 @@ def run_profile_case(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_1708_08739_gb300 as bcd
-    g, qs, _ = make_workload()
+    g, qs, _ = make_workload("rmat20_ef16_exact64")
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
     bcd.bc_set_config(dg, tile_words=args.tile_words, accumulation=args.accumulation or 1)
     r = int(gg.top_inout_vertices(g, 1)[0])
@@ -547,7 +666,7 @@ def run_set_experiment(args):
     __graft_entry__.build()
     import torch
     import paper_1708_08739_gb300 as bcd
-    g, _, _ = make_workload()
+    g, _, _ = make_workload("rmat20_ef16_exact64")
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
     bcd.bc_set_config(dg, tile_words=args.tile_words)
     sets = {k: [int(x) for x in gg.random_vertices(g.n, k, 200 + k)] for k in (5, 10, 15)}
@@ -580,7 +699,7 @@ def run_set_experiment(args):
                      "rv_size": {"avg": sum(rv) / k, "max": max(rv), "min": min(rv)},
                      "exact_queries": sum(1 for x in rv if x <= tau), "sources_run": info["sources_run"],
                      "one_at_a_time_s": t_one})
-    print(json.dumps({"experiment": "set", "graph": WORKLOADS[WORKLOAD].split(";")[0], "tau": tau,
+    print(json.dumps({"experiment": "set", "graph": WORKLOADS["rmat20_ef16_exact64"].split(";")[0], "tau": tau,
                       "exact_reference_s": t_exact, "rows": rows}), flush=True)
     dg.close()
 
@@ -592,8 +711,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tile-words", type=int, default=4)
-    ap.add_argument("--cpu-sources", type=int, default=256)
+    ap.add_argument("--cpu-budget-s", type=float, default=24.0,
+                    help="seconds of oracle work for the all-core CPU baseline (a third of it single-threaded)")
+    ap.add_argument("--ref-step-s", type=float, default=5.0, help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the R-MAT 20 exact batch and the serving run")
+    ap.add_argument("--serve-extra", type=int, default=512, help="queries of the serving run among the extras")
     ap.add_argument("--case", default="", choices=["", "profile", "wprofile"],
                     help="profile / wprofile: one small sampled batch on the unweighted / weighted R-MAT (for ncu), "
                          "no JSON bench line")

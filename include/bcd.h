@@ -49,7 +49,8 @@ typedef enum {
     BC_E_TIMEOUT = 6,          /* a bounded device wait gave up */
     BC_E_INTERNAL = 7,
     BC_E_BUSY = 8,             /* bc_submit: the server's queue is full; retry later */
-    BC_E_PENDING = 9           /* bc_poll: the query has not finished yet */
+    BC_E_PENDING = 9,          /* bc_poll: the query has not finished yet */
+    BC_E_CANCELLED = 10        /* bc_cancel stopped the call between two tiles */
 } bc_status;
 
 typedef enum { BC_MEM_HOST = 0, BC_MEM_DEVICE = 1 } bc_mem_kind;
@@ -222,8 +223,26 @@ bc_status bc_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *
                    bc_batch_info *info);
 
 /*
- * Parity probe: runs the single-source passes for up to 64 distinct
- * sources (one tile of the batched kernel) and returns, for each source
+ * One shard of bc_batch, for spreading a batch over several GPUs (one
+ * process and one graph replica per GPU): the sources of a group are
+ * independent terms of the sums of Algorithm 1 and 2 (and of the set version
+ * of Section 4.2), so shard k of nshards runs only tiles [T*k/nshards,
+ * T*(k+1)/nshards) of each group's T tiles, in the order bc_batch runs them,
+ * and out[i].bc receives that shard's part of query i's score (scaled by
+ * |RV(r)|/T for sampled queries). The scores of shards 0 .. nshards-1 add up
+ * to the bc_batch score (equal up to fp64 summation order); rv_size, samples
+ * and status are the same on every shard, and flags are to be OR-ed.
+ * Requires 0 <= shard < nshards, else BC_E_INVALID_ARG. nshards = 1 is
+ * bc_batch.
+ */
+bc_status bc_batch_shard(bc_graph *g, const bc_query *queries, int64_t nq, int32_t shard, int32_t nshards,
+                         bc_result *out, bc_batch_info *info);
+
+/*
+ * Parity probe: runs the single-source passes for 1 .. 64*w distinct
+ * sources (one tile of the batched kernel, w = tile_words on unweighted
+ * graphs, weighted_words on weighted ones; more is BC_E_INVALID_ARG) and
+ * returns, for each source
  * i and vertex v, dist[i*n + v] (UINT64_MAX when unreached; hop count for
  * an unweighted graph) and sigma[i*n + v] (fp64), and for each target
  * vertex t_j, dep[i*nt + j] = delta_{s_i}.(t_j) (Eq. 4). Any output may be
@@ -239,23 +258,30 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
  * the graph; while it exists, the graph must not be used by other calls.
  *
  * Admission: a submitted query waits until one of max_active query slots
- * (at most 64) is free and the number of admitted sources not yet run is
- * below max_pending_sources (each pending source holds a slot in the device
- * staging of the next slices; the dist/sigma/delta slabs themselves are per
- * tile and shared). Then its source set is prepared (RV(r); Philox draws for
- * sampled queries) and merged into the pool of pending sources: a source
- * already pending for another query is run once for both. The worker runs
- * the pool in slices of tiles_per_slice tiles, taking sources round-robin
- * across the active queries, so queries that arrive while others run get
- * their work into the next slice. Each result equals the single-query call
- * up to fp64 summation order.
+ * (at most 64) is free. Then its source set is prepared (RV(r); Philox draws
+ * for sampled queries) and it is admitted while the device bytes that its
+ * distinct sources hold until they have run (12 bytes each, 268 for a
+ * sampled query, which also stages its draw counts, plus 512 per tile of
+ * partial sums), added to those of the queries already admitted, stay within
+ * max_device_bytes; otherwise it returns to the head of the queue until
+ * running queries free their bytes, and a query whose bytes alone exceed the
+ * budget completes with status BC_E_BUSY. The per-(vertex, source) slabs
+ * (sigma, accumulators, masks, level history) are allocated once per graph
+ * for one tile and shared by all tiles, outside the budget. An admitted
+ * query's sources join the pool of pending sources: a source already pending
+ * for another query is run once for both. The worker runs the pool in slices
+ * of tiles_per_slice tiles, taking sources round-robin across the active
+ * queries, so queries that arrive while others run get their work into the
+ * next slice. Each result equals the single-query call up to fp64 summation
+ * order.
  */
 typedef struct bc_server bc_server;
 
 typedef struct {
     int32_t max_active;          /* query slots in flight, 1..64 (0: 64) */
     int32_t tiles_per_slice;     /* tiles per traversal launch (0: 16) */
-    int64_t max_pending_sources; /* admission bound on pending sources (0: 2^26) */
+    int64_t max_device_bytes;    /* admission budget in device bytes (0: a quarter of the
+                                    free device memory at bc_server_create) */
     int64_t max_queue;           /* bound on submitted, unadmitted queries (0: 2^20) */
 } bc_server_config;
 
@@ -330,6 +356,11 @@ void bc_server_destroy(bc_server *srv);
  *                  graphs. Results equal those of 1 up to fp64 rounding
  *                  order. On the R-MAT graphs of the benchmark a one-query
  *                  call runs about 1.4x faster.
+ *   timeout_us     limit, in microseconds of wall time, on every wait of a
+ *                  traversal kernel at a grid-wide barrier (default
+ *                  10,000,000: 10 s). A wait that runs out makes every block
+ *                  leave the kernel; the call returns BC_E_TIMEOUT, the
+ *                  graph's device state is reset and the handle stays usable.
  * Zero fields keep their current value.
  */
 typedef struct {
@@ -340,7 +371,7 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t weighted_words;
     int32_t accumulation;
-    int32_t reserved;
+    int32_t timeout_us;
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);
@@ -382,6 +413,28 @@ bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
 #define BC_NOALLOC_MAX_VERTICES 4194304
 bc_status bc_rv_compute_noalloc(const int64_t *d_roffsets, const int32_t *d_rcols, int32_t n, int32_t r,
                                 int32_t *d_out, int64_t cap, int64_t *count, void *stream);
+
+/*
+ * Cancels the call that is running on g (from another host thread; the one
+ * call that may overlap another on the same handle). The traversal kernels
+ * read the request when a tile of sources starts, so the running call stops
+ * within one tile, resets the graph's device state and returns
+ * BC_E_CANCELLED (bc_batch: every query of the stopped group gets that
+ * status). A request made while no call runs is dropped when the next call
+ * starts. The handle stays usable.
+ */
+bc_status bc_cancel(bc_graph *g);
+
+/*
+ * Fault injection on the host, for tests of the error paths: the k-th
+ * device allocation the library makes from now on (k >= 1, counted over all
+ * handles of the process) fails as if cudaMalloc had returned an
+ * out-of-memory error, so that call returns BC_E_OOM; k = 0 switches the
+ * injection off. A call that fails this way frees the handle's working
+ * memory, which the next call allocates again; the graph stays usable.
+ * k < 0 is BC_E_INVALID_ARG.
+ */
+bc_status bc_debug_fail_alloc(int64_t k);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char *bc_last_error(void);

@@ -28,6 +28,7 @@ BC_E_TIMEOUT = 6
 BC_E_INTERNAL = 7
 BC_E_BUSY = 8
 BC_E_PENDING = 9
+BC_E_CANCELLED = 10
 
 BC_MEM_HOST = 0
 BC_MEM_DEVICE = 1
@@ -76,11 +77,11 @@ class bc_batch_info(C.Structure):
 class bc_config(C.Structure):
     _fields_ = [("tile_words", C.c_int32), ("chunk_arcs", C.c_int32), ("block_threads", C.c_int32),
                 ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("weighted_words", C.c_int32),
-                ("accumulation", C.c_int32), ("reserved", C.c_int32)]
+                ("accumulation", C.c_int32), ("timeout_us", C.c_int32)]
 
 
 class bc_server_config(C.Structure):
-    _fields_ = [("max_active", C.c_int32), ("tiles_per_slice", C.c_int32), ("max_pending_sources", C.c_int64),
+    _fields_ = [("max_active", C.c_int32), ("tiles_per_slice", C.c_int32), ("max_device_bytes", C.c_int64),
                 ("max_queue", C.c_int64)]
 
 
@@ -108,6 +109,8 @@ _SIGNATURES = {
                                   C.POINTER(C.c_int64)]),
     "bc_batch": (C.c_int, [C.c_void_p, C.POINTER(bc_query), C.c_int64, C.POINTER(bc_result),
                            C.POINTER(bc_batch_info)]),
+    "bc_batch_shard": (C.c_int, [C.c_void_p, C.POINTER(bc_query), C.c_int64, C.c_int32, C.c_int32,
+                                 C.POINTER(bc_result), C.POINTER(bc_batch_info)]),
     "bc_spd_probe": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "bc_set_config": (C.c_int, [C.c_void_p, C.POINTER(bc_config)]),
@@ -119,6 +122,8 @@ _SIGNATURES = {
     "bc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(bc_result), C.POINTER(C.c_double), C.c_int64]),
     "bc_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(bc_server_stats)]),
     "bc_server_destroy": (None, [C.c_void_p]),
+    "bc_cancel": (C.c_int, [C.c_void_p]),
+    "bc_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "bc_last_error": (C.c_char_p, []),
     "bc_version": (C.c_char_p, []),
 }
@@ -223,18 +228,28 @@ def bc_set_stream(g: Graph, stream):
 
 
 def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0,
-                  weighted_words=0, accumulation=0):
+                  weighted_words=0, accumulation=0, timeout_us=0):
     c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm),
-                  int(weighted_words), int(accumulation))
+                  int(weighted_words), int(accumulation), int(timeout_us))
     _check(lib().bc_set_config(g.handle, C.byref(c)))
 
 
 def bc_get_config(g: Graph) -> dict:
     c = bc_config()
     _check(lib().bc_get_config(g.handle, C.byref(c)))
-    return {"tile_words": c.tile_words, "chunk_arcs": c.chunk_arcs, "block_threads": c.block_threads,
-            "source_order": c.source_order, "blocks_per_sm": c.blocks_per_sm, "weighted_words": c.weighted_words,
-            "accumulation": c.accumulation}
+    return {k: getattr(c, k) for k, _ in bc_config._fields_}
+
+
+def bc_cancel(g: Graph):
+    """Asks the call running on g (in another thread) to stop at its next
+    tile; that call then raises BCError with BC_E_CANCELLED."""
+    _check(lib().bc_cancel(g.handle))
+
+
+def bc_debug_fail_alloc(k: int):
+    """Makes the k-th device allocation of the library from now on fail
+    (BC_E_OOM); 0 switches the injection off."""
+    _check(lib().bc_debug_fail_alloc(int(k)))
 
 
 def bc_graph_info(g: Graph):
@@ -326,6 +341,18 @@ def bc_batch(g: Graph, specs):
     return out, {k: getattr(info, k) for k, _ in bc_batch_info._fields_}
 
 
+def bc_batch_shard(g: Graph, specs, shard: int, nshards: int):
+    """Shard `shard` of `nshards` of bc_batch: (list of result dicts whose
+    "bc" is this shard's part of each score, batch info dict)."""
+    q, nq = make_queries(specs)
+    res = (bc_result * max(nq, 1))()
+    info = bc_batch_info()
+    _check(lib().bc_batch_shard(g.handle, q, nq, int(shard), int(nshards), res, C.byref(info)))
+    out = [{"bc": res[i].bc, "status": res[i].status, "flags": res[i].flags, "rv_size": res[i].rv_size,
+            "samples": res[i].samples} for i in range(nq)]
+    return out, {k: getattr(info, k) for k, _ in bc_batch_info._fields_}
+
+
 def bc_spd_probe(g: Graph, sources, targets, want_dist=True, want_sigma=True, want_dep=True):
     """Per-source dist [nsrc, n] (uint64, 2**64-1 unreached), sigma [nsrc, n],
     dep [nsrc, nt] = delta_s.(t) and flags [nsrc] from one tile of the
@@ -345,8 +372,8 @@ def bc_spd_probe(g: Graph, sources, targets, want_dist=True, want_sigma=True, wa
 class Server:
     """Owning handle of a serving loop (bc_server) on a graph."""
 
-    def __init__(self, g: Graph, max_active=0, tiles_per_slice=0, max_pending_sources=0, max_queue=0):
-        cfg = bc_server_config(int(max_active), int(tiles_per_slice), int(max_pending_sources), int(max_queue))
+    def __init__(self, g: Graph, max_active=0, tiles_per_slice=0, max_device_bytes=0, max_queue=0):
+        cfg = bc_server_config(int(max_active), int(tiles_per_slice), int(max_device_bytes), int(max_queue))
         h = C.c_void_p()
         _check(lib().bc_server_create(g.handle, C.byref(cfg), C.byref(h)))
         self.handle = h

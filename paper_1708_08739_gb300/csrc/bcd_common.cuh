@@ -22,6 +22,7 @@ enum DevErr : int32_t {
     kDevTimeout = 4,
     kDevLevelOverflow = 5,
     kDevBucketOverflow = 6,
+    kDevCancelled = 7,
 };
 
 // Per-launch control block of the persistent traversal kernel.
@@ -141,6 +142,7 @@ struct TravParams {
     int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
     Counters *ctr;
     double timeout_ns;
+    const int32_t *cancel;   // host-mapped flag, non-zero: leave at the next tile start (may be NULL)
 };
 
 }  // namespace bcd
@@ -263,6 +265,9 @@ struct bc_graph {
     unsigned long long last_ns_other = 0;
     bcd::Counters last;                           // counters of the last traversal launch
     float last_ms_launch = 0;                // CUDA-event time of the last traversal launch
+    double timeout_ns = 10.0e9;              // limit on each grid-barrier wait
+    int32_t *cancel_h = nullptr;             // pinned, mapped host flag set by bc_cancel
+    int32_t *cancel_d = nullptr;             // ... its device address
 };
 
 namespace bcd {
@@ -313,16 +318,24 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
                     const std::vector<uint32_t> &mult, uint64_t exact_q, std::vector<double> &partials,
                     uint32_t *qflags, unsigned long long *edges);
 bc_status check_graph(bc_graph *g, const char *fn);
+void begin_call(bc_graph *g);
 bc_status prepare_ordering(bc_graph *g);
 // Tile order of a source: hop distance to the hub, then arcs two hops away (descending).
 int64_t source_order_key(const bc_graph *g, int32_t v);
 bc_status ensure_weighted_state(bc_graph *g);
 bc_status reset_dense_state(bc_graph *g);
 
+// Host-side fault injection (bc_debug_fail_alloc): true when this
+// allocation is the one chosen to fail.
+bool inject_alloc_failure();
+
 template <typename T>
 bc_status dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (inject_alloc_failure())
+        return set_error(BC_E_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                       " bytes failed (injected by bc_debug_fail_alloc)");
     cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();

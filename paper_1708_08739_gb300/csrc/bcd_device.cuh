@@ -47,7 +47,7 @@ __device__ inline bool grid_barrier(Counters *c, uint32_t &gen, double timeout_n
             while (ld_acquire(&c->bar_gen) == gen) {
                 if (ld_vol(&c->err) != 0) break;
                 ++spins;
-                if ((spins & 63) == 0 && (double)(global_ns() - t0) > timeout_ns) {
+                if ((double)(global_ns() - t0) > timeout_ns) {
                     set_err(c, kDevTimeout);
                     break;
                 }
@@ -64,6 +64,13 @@ __device__ inline bool grid_barrier(Counters *c, uint32_t &gen, double timeout_n
     }
     __syncthreads();
     return s_err == 0;
+}
+
+// Start of a tile: thread 0 of each block reads the host's cancel request
+// (bc_cancel); a request makes every block leave at the barrier that
+// follows, the same way as any other error.
+__device__ __forceinline__ void check_cancel(const TravParams &p) {
+    if (threadIdx.x == 0 && p.cancel && *(volatile const int32_t *)p.cancel != 0) set_err(p.ctr, kDevCancelled);
 }
 
 template <int W>

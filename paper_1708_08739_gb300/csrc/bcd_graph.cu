@@ -1,5 +1,6 @@
 // Graph residency: device copy of G, validation (Section 2 graph model) and
 // the reverse graph R(G) (Section 4.1, Def. 2), built once per graph.
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -20,6 +21,18 @@ bc_status cuda_error(cudaError_t e, const char *what) {
     cudaGetLastError();
     if (e == cudaErrorMemoryAllocation) return BC_E_OOM;
     return BC_E_CUDA;
+}
+
+// Countdown of bc_debug_fail_alloc: the allocation that takes it from 1 to 0
+// fails; 0 means off.
+static std::atomic<int64_t> g_fail_countdown{0};
+
+bool inject_alloc_failure() {
+    int64_t k = g_fail_countdown.load(std::memory_order_relaxed);
+    while (k > 0) {
+        if (g_fail_countdown.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) return k == 1;
+    }
+    return false;
 }
 
 namespace {
@@ -108,6 +121,9 @@ void bc_graph_destroy(bc_graph *g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     else cudaDeviceSynchronize();
     free_workspace(g);
+    if (g->cancel_h) cudaFreeHost(g->cancel_h);
+    g->cancel_h = nullptr;
+    g->cancel_d = nullptr;
     dev_free(g->d_off);
     dev_free(g->d_col);
     dev_free(g->d_w);
@@ -152,6 +168,8 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     }
     if (c->accumulation && c->accumulation != 1 && c->accumulation != 2)
         return set_error(BC_E_INVALID_ARG, "bc_set_config: accumulation must be 1 or 2");
+    if (c->timeout_us < 0) return set_error(BC_E_INVALID_ARG, "bc_set_config: timeout_us must be positive (0 keeps it)");
+    if (c->timeout_us) g->timeout_ns = 1000.0 * (double)c->timeout_us;
     if (c->accumulation) g->accumulation = c->accumulation;
     if (c->tile_words) g->tile_words = c->tile_words;
     if (c->chunk_arcs) g->chunk_arcs = c->chunk_arcs;
@@ -168,7 +186,20 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->blocks_per_sm = g->blocks_per_sm;
     c->weighted_words = g->weighted_words;
     c->accumulation = g->accumulation;
-    c->reserved = 0;
+    c->timeout_us = (int32_t)(g->timeout_ns / 1000.0);
+    return BC_OK;
+}
+
+bc_status bc_cancel(bc_graph *g) {
+    if (!g) return set_error(BC_E_INVALID_ARG, "bc_cancel: NULL graph");
+    if (!g->cancel_h) return set_error(BC_E_INTERNAL, "bc_cancel: the graph has no cancel flag");
+    __atomic_store_n(g->cancel_h, 1, __ATOMIC_SEQ_CST);
+    return BC_OK;
+}
+
+bc_status bc_debug_fail_alloc(int64_t k) {
+    if (k < 0) return set_error(BC_E_INVALID_ARG, "bc_debug_fail_alloc: k must be >= 0");
+    g_fail_countdown.store(k, std::memory_order_relaxed);
     return BC_OK;
 }
 
@@ -202,6 +233,15 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
     if (ce != cudaSuccess) return fail(cuda_error(ce, "cudaGetDevice"));
     ce = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (ce != cudaSuccess) return fail(cuda_error(ce, "cudaDeviceGetAttribute"));
+    // the cancel request of bc_cancel: a pinned host word the kernels read
+    // through its mapped device address
+    if ((ce = cudaHostAlloc((void **)&g->cancel_h, sizeof(int32_t), cudaHostAllocMapped)) != cudaSuccess) {
+        g->cancel_h = nullptr;
+        return fail(cuda_error(ce, "cudaHostAlloc of the cancel flag"));
+    }
+    *g->cancel_h = 0;
+    if ((ce = cudaHostGetDevicePointer((void **)&g->cancel_d, g->cancel_h, 0)) != cudaSuccess)
+        return fail(cuda_error(ce, "cudaHostGetDevicePointer of the cancel flag"));
     const size_t n1 = (size_t)d->n + 1, m = (size_t)d->m;
     if ((st = dev_alloc(&g->d_off, n1)) || (st = dev_alloc(&g->d_col, m)) || (st = dev_alloc(&g->d_roff, n1)) ||
         (st = dev_alloc(&g->d_rcol, m)))

@@ -226,14 +226,24 @@ bc_status alloc_levels(bc_graph *g, int64_t maxlev) {
 bc_status grow_levels(bc_graph *g) {
     const int64_t cur = g->ws.maxlev;
     if (cur >= (int64_t)INT32_MAX / 4) return set_error(BC_E_OOM, "traversal: more levels than the level arrays can hold");
-    return alloc_levels(g, std::min<int64_t>(cur * 4, (int64_t)INT32_MAX / 4));
+    const bc_status st = alloc_levels(g, std::min<int64_t>(cur * 4, (int64_t)INT32_MAX / 4));
+    if (st != BC_OK) free_workspace(g);
+    return st;
 }
 
 // Distance slab and bucket ring of the weighted kernel. A tile settles each
 // (vertex, source) pair once, so the history holds up to n * S entries.
+static bc_status build_weighted_state(bc_graph *g);
+
 bc_status ensure_weighted_state(bc_graph *g) {
+    if (g->ws.dist) return BC_OK;
+    const bc_status st = build_weighted_state(g);
+    if (st != BC_OK) free_workspace(g);
+    return st;
+}
+
+static bc_status build_weighted_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
-    if (ws.dist) return BC_OK;
     int R = 32;
     while ((uint32_t)R <= g->max_weight) R *= 2;
     if (R > 4096) return set_error(BC_E_INVALID_ARG, "weighted graphs need arc weights of at most 4095");
@@ -263,7 +273,11 @@ bc_status grow_buckets(bc_graph *g) {
     if (ws.bcap >= ((int64_t)1 << 34)) return set_error(BC_E_OOM, "bucket ring: too many pending pairs at one distance");
     dev_free(ws.buckets);
     ws.bcap *= 2;
-    BCD_TRY(dev_alloc(&ws.buckets, (size_t)ws.ring * (size_t)ws.bcap));
+    const bc_status st = dev_alloc(&ws.buckets, (size_t)ws.ring * (size_t)ws.bcap);
+    if (st != BC_OK) {
+        free_workspace(g);
+        return st;
+    }
     BCD_CUDA(cudaMemsetAsync(ws.bcount, 0, sizeof(unsigned long long) * 2 * (size_t)ws.ring, g->stream));
     return BC_OK;
 }
@@ -272,8 +286,10 @@ bc_status grow_history(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (ws.hcap >= (int64_t)INT32_MAX - 1 && ws.hmcap >= ws.hcap && ws.ccap >= ((int64_t)1 << 34))
         return set_error(BC_E_OOM, "level history exceeds 2^31 entries");
-    return alloc_history(g, std::min<int64_t>(ws.hcap * 2, (int64_t)INT32_MAX - 1), ws.ccap * 2, ws.pcap * 2,
-                         ws.hmcap * 2);
+    const bc_status st = alloc_history(g, std::min<int64_t>(ws.hcap * 2, (int64_t)INT32_MAX - 1), ws.ccap * 2,
+                                       ws.pcap * 2, ws.hmcap * 2);
+    if (st != BC_OK) free_workspace(g);
+    return st;
 }
 
 int tile_words_of(const bc_graph *g) { return g->weighted ? g->weighted_words : g->tile_words; }
@@ -328,9 +344,21 @@ void free_workspace(bc_graph *g) {
     ws = bcd_workspace();
 }
 
+static bc_status build_workspace(bc_graph *g, int W);
+
+// The working memory of a handle, allocated on first use. Any failure frees
+// all of it (no call can then meet a half-built workspace); the next call
+// allocates it again.
 bc_status ensure_workspace(bc_graph *g, int W) {
     bcd_workspace &ws = g->ws;
     if (ws.W >= W && ws.vs) return BC_OK;
+    const bc_status st = build_workspace(g, W);
+    if (st != BC_OK) free_workspace(g);
+    return st;
+}
+
+static bc_status build_workspace(bc_graph *g, int W) {
+    bcd_workspace &ws = g->ws;
     free_workspace(g);
     const int64_t n = g->n, m = g->m;
     ws.W = W;
@@ -595,7 +623,6 @@ static bc_status order_sources(bc_graph *g, int64_t nd) {
 
 static double samples_for(double eps, double delta) { return std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps)); }
 
-// Runs one group of at most 64 queries whose out-degree is positive.
 // d(r, t) and sigma_rt for every vertex t (the forward pass of Section 2 from
 // r alone), kept in rlev / rsig for the vertex scan: a scan-mode launch over
 // one tile whose only source is r. Its tile sums are not used (no query takes
@@ -640,7 +667,17 @@ static bc_status root_traversal(bc_graph *g, int32_t r) {
 
 static bool use_vertex_scan(const bc_graph *g, size_t nroots) { return g->accumulation == 2 && nroots == 1; }
 
-static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm) {
+// Tiles [lo, hi) of shard k out of nshards contiguous shards of ntiles tiles.
+static void shard_tiles(int64_t ntiles, int32_t k, int32_t nshards, int64_t *lo, int64_t *hi) {
+    *lo = ntiles * k / nshards;
+    *hi = ntiles * (k + 1) / nshards;
+}
+
+// Runs one group of at most 64 queries whose out-degree is positive; with
+// nshards > 1 only the group's tiles of shard k run, and each score is that
+// shard's part of the sum (already scaled by |RV| / T for sampled queries).
+static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm, int32_t shard,
+                           int32_t nshards) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
     const int nq = (int)qs.size();
@@ -721,6 +758,9 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     BCD_CUDA(cudaMemcpyAsync(&nd, d_cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaStreamSynchronize(s));
     const int64_t ntiles = (nd + S - 1) / S;
+    int64_t t_lo = 0, t_hi = ntiles;
+    shard_tiles(ntiles, shard, nshards, &t_lo, &t_hi);
+    const int64_t nrun = t_hi - t_lo;  // tiles this call runs
     if (g->source_order == 1 && ntiles >= 2) BCD_TRY(order_sources(g, nd));
     if (ntiles * S > nd) {
         fill_i32<<<1, 256, 0, s>>>(ws.dlist + nd, ntiles * S - nd, -1);
@@ -743,21 +783,40 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     VBit *d_qb = (VBit *)(ws.small + kSmallBits2);
     BCD_CUDA(cudaMemcpyAsync(d_qb, qb.data(), sizeof(VBit) * nq, cudaMemcpyHostToDevice, s));
     set_bits<<<1, 64, 0, s>>>(ws.qmask, d_qb, nq, 0);
-    BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
     g->launches += 1;
+    // the query bits must leave qmask on every exit (an error included), or a
+    // later group would read them as its own; a failed allocation may have
+    // freed the workspace, and qmask with it
+    struct QmaskGuard {
+        bc_graph *g;
+        std::vector<VBit> bits;
+        bool armed = true;
+        ~QmaskGuard() {
+            if (!armed || !g->ws.qmask || !g->ws.small) return;
+            VBit *d = (VBit *)(g->ws.small + kSmallBits2);
+            if (cudaMemcpyAsync(d, bits.data(), sizeof(VBit) * bits.size(), cudaMemcpyHostToDevice, g->stream) ==
+                cudaSuccess) {
+                set_bits<<<1, 64, 0, g->stream>>>(g->ws.qmask, d, (int)bits.size(), 1);
+                g->launches += 1;
+            }
+            cudaStreamSynchronize(g->stream);
+            cudaGetLastError();
+        }
+    } qguard{g, qb};
+    BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
     ev.rec(2);
     // batched SPD + dependencies over all tiles
     std::vector<double> sums(64, 0.0);
     std::vector<uint32_t> qflags(64, 0);
     int levels = 0;
     unsigned long long edges = 0;
-    const bool scan = ntiles > 0 && use_vertex_scan(g, roots.size());
+    const bool scan = nrun > 0 && use_vertex_scan(g, roots.size());
     if (scan) {
         BCD_TRY(root_traversal(g, roots[0]));
         tm.root = g->last_ms_launch;
     }
-    if (ntiles > 0) {
-        BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, ntiles * 64));
+    if (nrun > 0) {
+        BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, nrun * 64));
         TravParams p;
         memset(&p, 0, sizeof(p));
         p.mode = scan ? kModeScan : kModeSpd;
@@ -771,12 +830,12 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         }
         p.off = g->d_off;
         p.col = g->d_col;
-        p.srcs = ws.dlist;
-        p.ntiles = ntiles;
+        p.srcs = ws.dlist + t_lo * S;
+        p.ntiles = nrun;
         p.qmask = ws.qmask;
         p.need = ws.need;
         p.exact_q = exact_q;
-        p.mult = specs.empty() ? nullptr : ws.mult;
+        p.mult = specs.empty() ? nullptr : ws.mult + (size_t)t_lo * S * 64;
         p.qlevel = ws.qlevel;
         p.dep = ws.dep;
         p.tile_partial = ws.tile_partial;
@@ -793,13 +852,14 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         double *d_scale = (double *)(ws.small + kSmallTable);
         double *d_out = (double *)(ws.small + kSmallOut);
         BCD_CUDA(cudaMemcpyAsync(d_scale, scale.data(), 64 * sizeof(double), cudaMemcpyHostToDevice, s));
-        reduce_tiles<<<64, 256, 0, s>>>(ws.tile_partial, ntiles, d_scale, d_out);
+        reduce_tiles<<<64, 256, 0, s>>>(ws.tile_partial, nrun, d_scale, d_out);
         BCD_CUDA(cudaMemcpyAsync(sums.data(), d_out, 64 * sizeof(double), cudaMemcpyDeviceToHost, s));
         BCD_CUDA(cudaMemcpyAsync(qflags.data(), ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         g->launches += 1;
     }
     set_bits<<<1, 64, 0, s>>>(ws.qmask, d_qb, nq, 1);
     g->launches += 1;
+    qguard.armed = false;
     ev.rec(3);
     BCD_CUDA(cudaStreamSynchronize(s));
     BCD_CUDA(cudaGetLastError());
@@ -815,8 +875,8 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     tm.sample = ev.ms(1, 2);
     tm.spd = ev.ms(2, 3);
     tm.total = ev.ms(0, 3);
-    tm.sources = nd;
-    tm.tiles = ntiles;
+    tm.sources = nrun == ntiles ? nd : std::max<int64_t>(0, std::min(nd, t_hi * S) - t_lo * S);
+    tm.tiles = nrun;
     tm.edges = edges;
     tm.levels = levels;
     return BC_OK;
@@ -995,15 +1055,24 @@ int64_t source_order_key(const bc_graph *g, int32_t v) {
 
 bc_status prepare_ordering(bc_graph *g) { return g->source_order == 1 ? ensure_hub_levels(g) : BC_OK; }
 
+// A call starts: a cancel request left from before it is dropped.
+void begin_call(bc_graph *g) {
+    if (g->cancel_h) __atomic_store_n(g->cancel_h, 0, __ATOMIC_SEQ_CST);
+}
+
 bc_status check_graph(bc_graph *g, const char *fn) {
     if (!g) return set_error(BC_E_INVALID_ARG, std::string(fn) + ": NULL graph");
+    begin_call(g);
     BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     if (g->weighted) BCD_TRY(ensure_weighted_state(g));
     return BC_OK;
 }
 
-static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out, bc_batch_info *info) {
+static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *out, bc_batch_info *info,
+                           int32_t shard = 0, int32_t nshards = 1) {
     if (!g) return set_error(BC_E_INVALID_ARG, "bc_batch: NULL graph");
+    if (nshards < 1 || shard < 0 || shard >= nshards)
+        return set_error(BC_E_INVALID_ARG, "bc_batch_shard: need 0 <= shard < nshards");
     if (nq < 0 || (nq > 0 && (!queries || !out))) return set_error(BC_E_INVALID_ARG, "bc_batch: bad query array");
     BCD_TRY(check_graph(g, "bc_batch"));
     const int64_t launches0 = g->launches;
@@ -1014,7 +1083,7 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
     auto flush = [&]() -> bc_status {
         if (group.empty()) return BC_OK;
         GroupTimes t;
-        bc_status st = run_group(g, group, out, t);
+        bc_status st = run_group(g, group, out, t, shard, nshards);
         if (st != BC_OK) {
             for (auto &q : group) out[q.idx].status = st;
             group.clear();
@@ -1123,6 +1192,11 @@ bc_status bc_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_result *
     return run_batch(g, queries, nq, out, info);
 }
 
+bc_status bc_batch_shard(bc_graph *g, const bc_query *queries, int64_t nq, int32_t shard, int32_t nshards,
+                         bc_result *out, bc_batch_info *info) {
+    return run_batch(g, queries, nq, out, info, shard, nshards);
+}
+
 static bc_status single(bc_graph *g, const bc_query &q, double *bc, bc_info *info) {
     if (!bc) return set_error(BC_E_INVALID_ARG, "NULL result pointer");
     bc_result r;
@@ -1179,6 +1253,7 @@ bc_status bc_rv_compute(bc_graph *g, int32_t r, int32_t *out, int64_t cap, int64
     if (!g || !count) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: NULL argument");
     if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: vertex out of range");
     if (cap < 0 || (cap > 0 && !out)) return set_error(BC_E_INVALID_ARG, "bc_rv_compute: bad output buffer");
+    begin_call(g);
     BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     std::vector<int64_t> sizes;
     BCD_TRY(reach_roots(g, std::vector<int32_t>{r}, sizes));
@@ -1197,6 +1272,7 @@ bc_status bc_draw_samples(bc_graph *g, int32_t r, int64_t T, uint64_t seed, int3
     if (!g || !rv_size) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: NULL argument");
     if (r < 0 || r >= g->n) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: vertex out of range");
     if (T < 1 || T > 4000000000ll || !out) return set_error(BC_E_INVALID_ARG, "bc_draw_samples: bad T or output");
+    begin_call(g);
     BCD_TRY(ensure_workspace(g, tile_words_of(g)));
     *rv_size = 0;
     if (g->h_off[r + 1] == g->h_off[r]) return BC_OK;
@@ -1229,12 +1305,14 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
                        uint64_t *dist, double *sigma, double *dep, uint32_t *flags) {
     if (!g || (nsrc > 0 && !sources) || (nt > 0 && !targets))
         return set_error(BC_E_INVALID_ARG, "bc_spd_probe: NULL argument");
-    if (nsrc < 1 || nsrc > 64 || nt < 0 || nt > 64) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: 1..64 sources, 0..64 targets");
+    if (nt < 0 || nt > 64) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: 0..64 targets");
     BCD_TRY(check_graph(g, "bc_spd_probe"));
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
-    const int W = ws.W;  // probe tiles use the workspace width; slots past nsrc stay empty
+    const int W = tile_words_of(g);  // one tile of the graph's kernel; slots past nsrc stay empty
     const int S = 64 * W;
+    if (nsrc < 1 || nsrc > S)
+        return set_error(BC_E_INVALID_ARG, "bc_spd_probe: 1..64*tile_words sources (one tile of the kernel)");
     for (int i = 0; i < nsrc; ++i) {
         if (sources[i] < 0 || sources[i] >= g->n) return set_error(BC_E_INVALID_ARG, "bc_spd_probe: source out of range");
         for (int j = 0; j < i; ++j)
@@ -1366,7 +1444,7 @@ bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const 
                 for (int j = 0; j < nt; ++j) dep[(size_t)i * nt + j] = hd[i * 64 + j];
         }
     }
-    if (!qb.empty()) set_bits<<<1, 64, 0, s>>>(ws.qmask, d_nb + nb.size(), (int)qb.size(), 1);
+    if (!qb.empty() && ws.qmask) set_bits<<<1, 64, 0, s>>>(ws.qmask, d_nb + nb.size(), (int)qb.size(), 1);
     cudaStreamSynchronize(s);
     dev_free(d_nb);
     return st;

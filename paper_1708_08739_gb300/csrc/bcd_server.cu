@@ -2,15 +2,19 @@
 // over time).
 //
 // A worker thread owns the graph. Submitted queries wait in a queue until a
-// query slot (one of 64 mask bits) is free and the pending-source budget has
-// room; then their source sets are prepared (RV(r) by one reach traversal for
-// up to 64 roots, Philox draws for sampled queries) and join a pool of pending
-// sources. A source already pending for an earlier query is shared: the new
-// query's bit is added to it. The worker runs the pool in slices of tiles,
-// taking sources round-robin across the active queries, so that queries that
-// arrive while others are running get their tiles into the very next slice
-// and their work overlaps on the device. Each query sums its per-tile
-// partials in slice order and completes when its last source has run.
+// query slot (one of 64 mask bits) is free; then their source sets are
+// prepared (RV(r) by one reach traversal for up to 64 roots, Philox draws for
+// sampled queries). A prepared query is admitted while the device bytes that
+// its sources hold, added to those of the queries already admitted, fit the
+// server's byte budget; otherwise it goes back to the head of the queue until
+// others finish, and a query that alone exceeds the budget is answered with
+// BC_E_BUSY. An admitted query's sources join a pool of pending sources: a
+// source already pending for an earlier query is shared (the new query's bit
+// is added to it). The worker runs the pool in slices of tiles, taking sources
+// round-robin across the active queries, so that queries that arrive while
+// others are running get their tiles into the very next slice and their work
+// overlaps on the device. Each query sums its per-tile partials in slice order
+// and completes when its last source has run.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -42,6 +46,7 @@ struct SQuery {
     bool done = false;
     std::deque<int32_t> pending;                 // sources not yet run
     std::unordered_map<int32_t, uint32_t> mult;  // draw counts (sampled)
+    int64_t bytes = 0;                           // device bytes its sources hold (staged_bytes)
     Clock::time_point t_submit, t_done;
     bc_result res{};
 };
@@ -49,6 +54,18 @@ struct SQuery {
 double samples_for(double eps, double delta) { return std::ceil(std::log(2.0 / delta) / (2.0 * eps * eps)); }
 
 }  // namespace
+
+// Device bytes that a query's distinct sources hold from admission until they
+// have run: per source, its slot in the union list (4 bytes), its query mask
+// (8 bytes) and, for a sampled query, its row of draw counts (64 x 4 bytes);
+// per tile of S sources, the tile's per-query partial sums (64 x 8 bytes).
+// The per-(vertex, source) slabs (sigma, accumulators, masks, level history)
+// are allocated once per graph for one tile and reused by every tile, so they
+// are the server's fixed cost, outside the budget.
+int64_t bcd_staged_bytes(int64_t sources, bool sampled, int S) {
+    const int64_t per = 4 + 8 + (sampled ? 64 * 4 : 0);
+    return sources * per + (sources + S - 1) / S * 64 * 8;
+}
 
 struct bc_server {
     bc_graph *g = nullptr;
@@ -60,19 +77,21 @@ struct bc_server {
     uint64_t next_ticket = 1;
     std::deque<SQuery *> queue;
     std::unordered_map<uint64_t, SQuery *> tickets;
+    bc_server_stats stats{};  // guarded by mu
     // worker-owned state
     SQuery *slots[64] = {};
     int nactive = 0;
-    int rr = 0;                                     // round-robin cursor over slots
-    int64_t pending_sources = 0;
+    int rr = 0;                                       // round-robin cursor over slots
+    int64_t held_bytes = 0;                           // sum of the admitted queries' bytes
+    int64_t defer_held = -1;                          // held_bytes when the queue head was deferred
     std::unordered_map<int32_t, uint64_t> pend_need;  // pending source -> slots that need it
-    bc_server_stats stats{};
     bc_status fatal = BC_OK;
 
     void run();
     bool admit();
     bool run_slice_once();
     void complete(SQuery *q, int32_t status);
+    void fail_active(int32_t status);
 };
 
 void bc_server::complete(SQuery *q, int32_t status) {
@@ -82,8 +101,12 @@ void bc_server::complete(SQuery *q, int32_t status) {
     q->res.rv_size = q->rv;
     q->res.samples = (q->sampled && q->rv > 0) ? q->T : 0;
     q->pending.clear();
+    held_bytes -= q->bytes;
+    q->bytes = 0;
     if (q->slot >= 0) {
-        bcd::set_query_bit(g, q->q.r, q->slot, false);
+        // a failed allocation may have freed the workspace (and the query
+        // masks with it)
+        if (g->ws.qmask) bcd::set_query_bit(g, q->q.r, q->slot, false);
         slots[q->slot] = nullptr;
         --nactive;
         q->slot = -1;
@@ -92,17 +115,29 @@ void bc_server::complete(SQuery *q, int32_t status) {
     q->t_done = Clock::now();
     q->done = true;
     stats.completed += 1;
+    stats.active = nactive;
     cv_done.notify_all();
 }
 
+// Every active query ends with status (a slice failed, or the workspace that
+// held their query masks was freed); their pending sources leave the pool.
+void bc_server::fail_active(int32_t status) {
+    for (int s = 0; s < 64; ++s)
+        if (slots[s]) complete(slots[s], status);
+    pend_need.clear();
+}
+
 // Moves queued queries into free slots, prepares their sources, and merges
-// them into the pending pool. Returns true if anything was admitted.
+// them into the pending pool while their bytes fit the budget. Returns true
+// if any query left the queue.
 bool bc_server::admit() {
+    // a deferred head waits until running queries have freed some bytes
+    if (defer_held >= 0 && nactive > 0 && held_bytes >= defer_held) return false;
+    defer_held = -1;
     std::vector<SQuery *> batch;
     {
         std::lock_guard<std::mutex> lk(mu);
-        while (!queue.empty() && nactive + (int)batch.size() < cfg.max_active &&
-               pending_sources < cfg.max_pending_sources) {
+        while (!queue.empty() && nactive + (int)batch.size() < cfg.max_active && held_bytes < cfg.max_device_bytes) {
             batch.push_back(queue.front());
             queue.pop_front();
         }
@@ -129,8 +164,11 @@ bool bc_server::admit() {
     bc_status st = bcd::prepare_sources(g, items);
     if (st != BC_OK) {
         for (SQuery *q : prepq) complete(q, st);
+        if (!g->ws.qmask) fail_active(st);
         return true;
     }
+    const int S = 64 * bcd::tile_words_of(g);
+    std::vector<SQuery *> deferred;
     for (size_t i = 0; i < prepq.size(); ++i) {
         SQuery *q = prepq[i];
         bcd::PrepItem &it = items[i];
@@ -140,11 +178,24 @@ bool bc_server::admit() {
             complete(q, BC_OK);
             continue;
         }
+        const int64_t bytes = bcd_staged_bytes((int64_t)it.srcs.size(), q->sampled, S);
+        if (bytes > cfg.max_device_bytes) {
+            // could never fit, even alone
+            bcd::set_error(BC_E_BUSY, "bc_server: the query's sources need more device bytes than the budget");
+            complete(q, BC_E_BUSY);
+            continue;
+        }
+        if (held_bytes + bytes > cfg.max_device_bytes) {
+            deferred.push_back(q);  // waits for running queries to free their bytes
+            continue;
+        }
         int slot = 0;
         while (slots[slot]) ++slot;
         slots[slot] = q;
         q->slot = slot;
         ++nactive;
+        q->bytes = bytes;
+        held_bytes += bytes;
         if (bcd::set_query_bit(g, q->q.r, slot, true) != BC_OK) {
             complete(q, BC_E_CUDA);
             continue;
@@ -161,10 +212,17 @@ bool bc_server::admit() {
             if (q->sampled) q->mult[v] = it.mult[k];
         }
         q->outstanding = (int64_t)it.srcs.size();
-        pending_sources += q->outstanding;
+        std::lock_guard<std::mutex> lk(mu);
         stats.admitted += 1;
+        stats.active = nactive;
     }
-    return true;
+    if (!deferred.empty()) {
+        // back to the head of the queue, in their order (prepared again later)
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) queue.push_front(*it);
+        defer_held = held_bytes;
+    }
+    return deferred.size() < prepq.size() || prepq.size() < batch.size();
 }
 
 // Runs one slice of tiles from the pending pool. Returns false when idle.
@@ -230,14 +288,16 @@ bool bc_server::run_slice_once() {
     unsigned long long edges = 0;
     const auto t0 = Clock::now();
     bc_status st = bcd::run_slice(g, srcs, needs, mult, exact_q, partials, qflags, &edges);
-    stats.busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
-    stats.slices += 1;
-    stats.sources_run += (int64_t)take.size();
-    stats.edges_traversed += (int64_t)edges;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stats.busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+        stats.slices += 1;
+        stats.sources_run += (int64_t)take.size();
+        stats.edges_traversed += (int64_t)edges;
+    }
     if (st != BC_OK) {
         fatal = st;
-        for (int s = 0; s < 64; ++s)
-            if (slots[s]) complete(slots[s], st);
+        fail_active(st);
         return true;
     }
     for (int s = 0; s < 64; ++s) {
@@ -254,7 +314,6 @@ bool bc_server::run_slice_once() {
             if (slots[b]) slots[b]->outstanding -= 1;
         }
     }
-    pending_sources -= (int64_t)take.size();
     for (int s = 0; s < 64; ++s)
         if (slots[s] && slots[s]->outstanding <= 0) complete(slots[s], BC_OK);
     return true;
@@ -274,8 +333,7 @@ void bc_server::run() {
         (void)did;
     }
     // fail whatever is left
-    for (int s = 0; s < 64; ++s)
-        if (slots[s]) complete(slots[s], BC_E_INTERNAL);
+    fail_active(BC_E_INTERNAL);
 }
 
 using namespace bcd;
@@ -290,16 +348,25 @@ bc_status bc_server_create(bc_graph *g, const bc_server_config *cfg, bc_server *
     s->g = g;
     s->cfg.max_active = 64;
     s->cfg.tiles_per_slice = 16;
-    s->cfg.max_pending_sources = 1ll << 26;
     s->cfg.max_queue = 1 << 20;
+    {
+        // default budget: a quarter of the device memory free once the
+        // graph's workspace exists
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = (size_t)1 << 30;
+        }
+        s->cfg.max_device_bytes = std::max<int64_t>((int64_t)(fr / 4), 1 << 20);
+    }
     if (cfg) {
         if (cfg->max_active) s->cfg.max_active = cfg->max_active;
         if (cfg->tiles_per_slice) s->cfg.tiles_per_slice = cfg->tiles_per_slice;
-        if (cfg->max_pending_sources) s->cfg.max_pending_sources = cfg->max_pending_sources;
+        if (cfg->max_device_bytes) s->cfg.max_device_bytes = cfg->max_device_bytes;
         if (cfg->max_queue) s->cfg.max_queue = cfg->max_queue;
     }
     if (s->cfg.max_active < 1 || s->cfg.max_active > 64 || s->cfg.tiles_per_slice < 1 || s->cfg.max_queue < 1 ||
-        s->cfg.max_pending_sources < 1) {
+        s->cfg.max_device_bytes < 1) {
         delete s;
         return set_error(BC_E_INVALID_ARG, "bc_server_create: config out of range");
     }
@@ -370,7 +437,6 @@ bc_status bc_server_stats_get(bc_server *s, bc_server_stats *st) {
     if (!s || !st) return set_error(BC_E_INVALID_ARG, "bc_server_stats_get: NULL argument");
     std::lock_guard<std::mutex> lk(s->mu);
     *st = s->stats;
-    st->active = s->nactive;
     st->queued = (int64_t)s->queue.size();
     return BC_OK;
 }

@@ -595,6 +595,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
 
     for (long long tile = 0; tile < p.ntiles; ++tile) {
         const int32_t *tsrc = p.srcs + tile * S;
+        check_cancel(p);
         if (blockIdx.x == 0) init_tile<W, MODE>(p, tsrc);
         for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
@@ -825,6 +826,7 @@ bc_status launch(bc_graph *g, TravParams &p) {
 
 bc_status reset_dense_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
+    if (!ws.vs) return BC_OK;  // no workspace (never built, or freed after a failure)
     BCD_CUDA(cudaMemsetAsync(ws.vs, 0, sizeof(uint64_t) * (size_t)ws.n * ws.vs_stride, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.tag, 0xff, sizeof(int32_t) * (size_t)ws.n, g->stream));
     BCD_CUDA(cudaMemsetAsync(ws.sigma, 0, sizeof(double) * (size_t)ws.n * 64 * ws.W, g->stream));
@@ -869,7 +871,8 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.ctr = ws.ctr;
         p.n = g->n;
         p.chunk_arcs = g->chunk_arcs;
-        p.timeout_ns = 10.0e9;
+        p.timeout_ns = g->timeout_ns;
+        p.cancel = g->cancel_d;
         BCD_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), g->stream));
         bc_status st = BC_E_INTERNAL;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -941,6 +944,10 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         if (c.err == kDevTimeout) {
             reset_dense_state(g);
             return set_error(BC_E_TIMEOUT, "traversal: a grid barrier wait timed out");
+        }
+        if (c.err == kDevCancelled) {
+            reset_dense_state(g);
+            return set_error(BC_E_CANCELLED, "traversal: cancelled by bc_cancel");
         }
         if (c.err == kDevBucketOverflow) {
             // more pending pairs at one distance than a ring slot holds: grow and rerun

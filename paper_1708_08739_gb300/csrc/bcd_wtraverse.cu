@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
 
     for (long long tile = 0; tile < p.ntiles; ++tile) {
         const int32_t *tsrc = p.srcs + tile * S;
+        check_cancel(p);
         if (blockIdx.x == 0) {
             for (int t = threadIdx.x; t < S; t += blockDim.x) {
                 const int v = tsrc[t];

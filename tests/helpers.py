@@ -128,3 +128,18 @@ def random_digraph(n, p, seed, weighted=False, wmax=4):
     arcs = [(u, v) for u in range(n) for v in range(n) if u != v and r.random() < p]
     weights = [int(x) for x in r.integers(1, wmax + 1, size=len(arcs))] if weighted else None
     return csr(n, arcs, weights)
+
+
+REL = 1e-9
+
+
+def close(a, b, rel=REL):
+    """The parity bar for fp64 scores and dependencies: |a - b| <= rel * |b|,
+    a purely relative bound (every delta and BC is a sum of non-negative
+    terms, so its rounding error is relative too); a reference value of
+    exactly 0 (no source reaches past r) must be matched exactly."""
+    a = float(a)
+    b = float(b)
+    if b == 0.0:
+        return a == 0.0
+    return abs(a - b) <= rel * abs(b)

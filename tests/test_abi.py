@@ -96,3 +96,14 @@ def test_binding_struct_layouts_match_the_header(built_lib, tmp_path):
             assert getattr(py, field).offset == int(value), (name, field)
         seen += 1
     assert seen == sum(1 + len(getattr(built_lib, n)._fields_) for n in STRUCTS)
+
+
+def test_host_only_argument_checks(built_lib):
+    """Calls whose argument checks run on the host before any device work."""
+    b = built_lib
+    with pytest.raises(b.BCError) as e:
+        b.bc_debug_fail_alloc(-1)
+    assert e.value.status == b.BC_E_INVALID_ARG
+    b.bc_debug_fail_alloc(0)
+    assert b.lib().bc_cancel(None) == b.BC_E_INVALID_ARG
+    assert b.lib().bc_set_config(None, None) == b.BC_E_INVALID_ARG

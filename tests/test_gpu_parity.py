@@ -10,11 +10,10 @@ import pytest
 
 import graphgen as gg
 import oracle as O
-from helpers import csr
+from helpers import csr, close
 
 pytestmark = pytest.mark.gpu
 
-REL = 1e-9
 UNREACHED = np.iinfo(np.uint64).max
 
 
@@ -23,10 +22,6 @@ def bcd():
     import paper_1708_08739_gb300 as m
     m.lib()
     return m
-
-
-def close(a, b, rel=REL):
-    return abs(a - b) <= rel * max(1.0, abs(b))
 
 
 def make(bcd, g, **cfg):
@@ -386,3 +381,43 @@ def test_device_input_arrays(bcd, er1):
     dg = bcd.bc_graph_create(g.n, off, col)
     r = 11
     assert close(bcd.bc_exact(dg, r)[0], O.bc_exact(og, r, 0)[0])
+
+
+@pytest.mark.parametrize("nshards", [1, 2, 3, 5])
+def test_batch_shards_add_up(bcd, er1, nshards):
+    """bc_batch_shard: the shards' partial scores of a mixed batch (exact,
+    sampled, hybrid; 128-source tiles, so each group has several tiles) add
+    up, in shard order, to the oracle's scores; rv_size, samples and status
+    agree on every shard."""
+    from paper_1708_08739_gb300 import shard as sh
+    g, og = er1
+    dg = make(bcd, g, tile_words=2)
+    rs = gg.random_vertices(g.n, 12, 41).tolist()
+    specs = []
+    for i, r in enumerate(rs):
+        if i % 3 == 0:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_EXACT})
+        elif i % 3 == 1:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 900, "seed": 7})
+        else:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_HYBRID, "T": 1000, "seed": 3})
+    parts = {}
+    outs = []
+    for k in range(nshards):
+        out, info = bcd.bc_batch_shard(dg, specs, k, nshards)
+        parts[k] = [o["bc"] for o in out]
+        outs.append(out)
+    tot = sh.reduce_in_shard_order(parts, nshards, len(specs))
+    for i, s in enumerate(specs):
+        r = s["r"]
+        rvk = O.rv(og, r).shape[0]
+        if s["kind"] == bcd.BC_QUERY_EXACT or (s["kind"] == bcd.BC_QUERY_HYBRID and rvk <= s["T"]):
+            want = O.bc_exact(og, r, 0)[0]
+        else:
+            want = O.bc_approx(og, r, s["T"], s["seed"], 0)[0]
+        assert close(tot[i], want), (nshards, s, tot[i], want)
+        for out in outs:
+            assert out[i]["status"] == 0 and out[i]["rv_size"] == outs[0][i]["rv_size"]
+            assert out[i]["samples"] == outs[0][i]["samples"]
+    with pytest.raises(bcd.BCError):
+        bcd.bc_batch_shard(dg, specs, nshards, nshards)

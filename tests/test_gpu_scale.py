@@ -5,28 +5,28 @@ R-MAT scale 20 (the exact batch): RV lists of all 64 queries bit-exact;
 dist and sigma of sampled union sources bit-exact and their dependencies on
 every query within 1e-9; full BC(r) for the queries the oracle can finish;
 the vertex-scan accumulation on single queries.
+A whole 256-source tile probed element by element.
 R-MAT scale 22 with 30 % reciprocal arcs (the sampled batch): the draws of
-eps = 0.01, delta = 0.1, seed 7 bit-exact, and the dependencies of drawn
-sources within 1e-9.
+eps = 0.01, delta = 0.1, seed 7 bit-exact, the dependencies of drawn
+sources within 1e-9, and four of its sampled queries end to end (T = 128)
+against the oracle's A-BCD on the same draws.
 The R-MAT scale 20 graph with weights uniform in [1, 255] (seed 3; the
 weighted batch of 32 uniform queries, seed 104), in the default weighted tile
 width: RV lists bit-exact, uint64 distances and sigma of sampled sources
 bit-exact and their dependencies on all 32 queries within 1e-9, the
 queries with empty RV answered 0, and the vertex scan on a sampled query.
 """
+import concurrent.futures as cf
+import os
+
 import numpy as np
 import pytest
 
 import graphgen as gg
 import oracle as O
+from helpers import close
 
 pytestmark = pytest.mark.gpu
-
-REL = 1e-9
-
-
-def close(a, b):
-    return abs(a - b) <= REL * max(1.0, abs(b))
 
 
 @pytest.fixture(scope="module")
@@ -89,20 +89,23 @@ def test_rmat20_small_queries_full(bcd, rmat20):
 
 
 def test_rmat20_vertex_scan(bcd, rmat20):
-    """accumulation = 2 at full size, one query per call: 96 draws on the top
-    in*out vertex (seed 7) against the oracle on the same draws; the bench's
-    14,979-draw query against the Eq. 4 path; the small exact queries against
-    the oracle."""
+    """accumulation = 2 at full size, one query per call: 96 and 512 draws on
+    the top in*out vertex (seed 7) against the oracle on the same draws, both
+    accumulations; the small exact queries against the oracle."""
     g, og, dg, qs = rmat20
     top = qs[32]
-    want, _, k, _ = O.bc_approx(og, top, 96, 7, 0)
+    threads = os.cpu_count() or 1
+    want96, _, k, _ = O.bc_approx(og, top, 96, 7, threads)
+    want512, _, k512, _ = O.bc_approx(og, top, 512, 7, threads)
+    assert k512 == k
     bcd.bc_set_config(dg, accumulation=2)
     try:
         out, info = bcd.bc_batch(dg, [{"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 96, "seed": 7}])
         assert info["scan_pairs"] > 0 and out[0]["rv_size"] == k
-        assert close(out[0]["bc"], want), (out[0]["bc"], want)
-        big = {"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 14979, "seed": 7}
-        scan, _ = bcd.bc_batch(dg, [big])
+        assert close(out[0]["bc"], want96), (out[0]["bc"], want96)
+        scan, info = bcd.bc_batch(dg, [{"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 512, "seed": 7}])
+        assert info["scan_pairs"] > 0
+        assert close(scan[0]["bc"], want512), (scan[0]["bc"], want512)
         small = []
         for r in dict.fromkeys(qs):
             kk = bcd.bc_rv_compute(dg, r).shape[0]
@@ -113,9 +116,35 @@ def test_rmat20_vertex_scan(bcd, rmat20):
             assert close(got, O.bc_exact(og, r, 0)[0]), r
     finally:
         bcd.bc_set_config(dg, accumulation=1)
-    push, info = bcd.bc_batch(dg, [big])
+    push, info = bcd.bc_batch(dg, [{"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 512, "seed": 7}])
     assert info["scan_pairs"] == 0
-    assert close(scan[0]["bc"], push[0]["bc"]), (scan[0]["bc"], push[0]["bc"])
+    assert close(push[0]["bc"], want512), (push[0]["bc"], want512)
+
+
+def test_rmat20_full_tile_probe(bcd, rmat20):
+    """One whole 256-source tile of the bench's kernel (slots 0..255), element
+    by element: every source's distances and sigma bit-exact, and its
+    dependencies on the 64 query vertices within the relative bar."""
+    g, og, dg, qs = rmat20
+    S = 64 * bcd.bc_get_config(dg)["tile_words"]
+    assert S == 256
+    union = O.rv(og, qs[32])
+    rng = np.random.default_rng(9)
+    srcs = np.sort(rng.choice(union, size=S, replace=False)).astype(np.int32)
+    qv = np.array(list(dict.fromkeys(qs)), dtype=np.int32)[:64]
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, qv)
+    threads = os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        # the oracle's C code releases the GIL: sources run in parallel
+        states = ex.map(lambda s: (s, O.source_state(og, int(s))), srcs.tolist())
+        for i, (s, st) in enumerate(states):
+            assert np.array_equal(dist[i], st["dist"]), (i, s)
+            assert (flags[i] != 0) == (st["flags"] != 0), (i, s)
+            if not st["flags"]:
+                assert np.array_equal(sig[i], st["sigma"]), (i, s)
+            for j, t in enumerate(qv.tolist()):
+                if t != s:
+                    assert close(dep[i, j], st["delta"][t]), (i, s, t, dep[i, j], st["delta"][t])
 
 
 @pytest.fixture(scope="module")
@@ -152,6 +181,31 @@ def test_rmat22_sampled_draws_and_dependencies(bcd, rmat22):
                 assert close(dep[i, 0], odep[i, 0]), (int(srcs[i]), dep[i, 0], odep[i, 0])
             checked += 1
     assert checked == 1
+
+
+def test_rmat22_sampled_batch_end_to_end(bcd, rmat22):
+    """The bench's sampled R-MAT 22 batch shape end to end: the first four of
+    the 64 uniform queries (seed 105) whose RV holds more than 1000 sources,
+    A-BCD with T = 128 draws (Philox seed 7) in one bc_batch, each bc(r)
+    against the oracle's A-BCD on the same draws (128 draws keep the oracle's
+    four runs of Brandes from 128 sources on 42.7 M arcs to about a minute)."""
+    g, og, dg = rmat22
+    qs = [int(x) for x in gg.random_vertices(g.n, 64, 105)]
+    big = []
+    for r in qs:
+        if g.out_degree()[r] > 0 and r not in big and bcd.bc_rv_compute(dg, r).shape[0] > 1000:
+            big.append(r)
+        if len(big) == 4:
+            break
+    assert len(big) == 4
+    T = 128
+    specs = [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": T, "seed": 7} for r in big]
+    out, info = bcd.bc_batch(dg, specs)
+    threads = os.cpu_count() or 1
+    for r, o in zip(big, out):
+        want, draws, k, f = O.bc_approx(og, r, T, 7, threads)
+        assert o["status"] == 0 and o["rv_size"] == k and o["samples"] == T
+        assert close(o["bc"], want), (r, o["bc"], want)
 
 
 @pytest.fixture(scope="module")

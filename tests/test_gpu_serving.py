@@ -8,14 +8,9 @@ import pytest
 
 import graphgen as gg
 import oracle as O
+from helpers import close
 
 pytestmark = pytest.mark.gpu
-
-REL = 1e-9
-
-
-def close(a, b):
-    return abs(a - b) <= REL * max(1.0, abs(b))
 
 
 @pytest.fixture(scope="module")
@@ -106,3 +101,42 @@ def test_server_rejects_and_drains(setup):
     assert len(ts) + busy == 30
     for s, bc in results:  # the graph is free again once the server is closed
         assert close(bc, alone(bcd, dg, s))
+
+
+def test_server_memory_budget(setup):
+    """Admission by device bytes: with a budget of 8 KiB an exact query whose
+    RV holds more than a few hundred sources can never fit and completes
+    with BC_E_BUSY, while small queries are admitted (two that do not fit
+    together run one after the other) and answer as alone."""
+    bcd, g, og, _ = setup
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    sizes = {}
+    for r in gg.random_vertices(g.n, 400, 77).tolist() + gg.top_inout_vertices(g, 2).tolist():
+        if g.out_degree()[r] > 0 and r not in sizes:
+            sizes[r] = bcd.bc_rv_compute(dg, r).shape[0]
+    big = max(sizes, key=sizes.get)
+    assert sizes[big] > 1000
+    small = [r for r, k in sizes.items() if 100 <= k <= 300][:2]
+    assert len(small) == 2, sizes
+    budget = 8192
+    srv = bcd.Server(dg, max_device_bytes=budget)
+    try:
+        tb = srv.submit({"r": big, "kind": bcd.BC_QUERY_EXACT})
+        ts = [srv.submit({"r": r, "kind": bcd.BC_QUERY_EXACT}) for r in small]
+        res = {}
+        deadline = time.time() + 120
+        while len(res) < 3 and time.time() < deadline:
+            for t in [tb] + ts:
+                if t not in res:
+                    x = srv.poll(t, timeout_us=2000)
+                    if x is not None:
+                        res[t] = x[0]
+        assert len(res) == 3
+        assert res[tb]["status"] == bcd.BC_E_BUSY
+        for t, r in zip(ts, small):
+            want = O.bc_exact(og, r, 0)[0]
+            assert res[t]["status"] == 0 and res[t]["rv_size"] == sizes[r]
+            assert close(res[t]["bc"], want), (r, res[t]["bc"], want)
+        assert srv.stats()["admitted"] == 2
+    finally:
+        srv.close()

@@ -17,11 +17,9 @@ import pytest
 
 import graphgen as gg
 import oracle as O
-from helpers import csr
+from helpers import csr, close
 
 pytestmark = pytest.mark.gpu
-
-REL = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -29,10 +27,6 @@ def bcd():
     import paper_1708_08739_gb300 as m
     m.lib()
     return m
-
-
-def close(a, b, rel=REL):
-    return abs(a - b) <= rel * max(1.0, abs(b))
 
 
 def make(bcd, g, **cfg):
