@@ -447,7 +447,7 @@ def run_extras(args, bcd, dg22, g22, stream):
             bcd.bc_batch(dg22, [s])
         one = 32 / (time.time() - t)
         out["serving"] = {
-            "workload": "R-MAT 22 + 30% reciprocal resident; %d Zipf(1.1) queries alternating exact (|RV| <= %d) "
+            "workload": "R-MAT 22 + 30%% reciprocal resident; %d Zipf(1.1) queries alternating exact (|RV| <= %d) "
                         "and sampled (eps 0.02, delta 0.1, seed 7)" % (len(specs_s), args.serve_rv_max),
             "closed_loop": {"queries_per_s": sat, "p50_ms": float(np.percentile(lat, 50)),
                             "p99_ms": float(np.percentile(lat, 99))},

@@ -1168,7 +1168,9 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
     if (st != BC_OK) worst = st;
     bi.launches = g->launches - launches0;
     if (info) *info = bi;
-    if (worst == BC_E_CUDA || worst == BC_E_OOM || worst == BC_E_TIMEOUT || worst == BC_E_INTERNAL) return worst;
+    if (worst == BC_E_CUDA || worst == BC_E_OOM || worst == BC_E_TIMEOUT || worst == BC_E_INTERNAL ||
+        worst == BC_E_CANCELLED)
+        return worst;
     return BC_OK;
 }
 

@@ -104,21 +104,29 @@ def test_server_rejects_and_drains(setup):
 
 
 def test_server_memory_budget(setup):
-    """Admission by device bytes: with a budget of 8 KiB an exact query whose
-    RV holds more than a few hundred sources can never fit and completes
-    with BC_E_BUSY, while small queries are admitted (two that do not fit
-    together run one after the other) and answer as alone."""
-    bcd, g, og, _ = setup
+    """Admission by device bytes, on a sparse ER graph (3,000 vertices,
+    3,600 arcs: RV sizes from 1 to about 850). The budget fits either of two
+    small exact queries but not both, and not the big one: the big query
+    completes with BC_E_BUSY, the two small ones run one after the other and
+    answer as alone."""
+    bcd = setup[0]
+    g = gg.erdos_renyi(3000, 3600, 2)
+    og = O.Graph.from_csr(g)
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    S = 64 * bcd.bc_get_config(dg)["tile_words"]
     sizes = {}
-    for r in gg.random_vertices(g.n, 400, 77).tolist() + gg.top_inout_vertices(g, 2).tolist():
-        if g.out_degree()[r] > 0 and r not in sizes:
+    for r in range(0, g.n, 7):
+        if g.out_degree()[r] > 0:
             sizes[r] = bcd.bc_rv_compute(dg, r).shape[0]
     big = max(sizes, key=sizes.get)
-    assert sizes[big] > 1000
-    small = [r for r, k in sizes.items() if 100 <= k <= 300][:2]
-    assert len(small) == 2, sizes
-    budget = 8192
+    small = [r for r, k in sizes.items() if 50 <= k <= 110][:2]
+    assert sizes[big] > 700 and len(small) == 2, sizes
+
+    def staged(k):  # the header's count: 12 bytes per source, 512 per tile
+        return 12 * k + (k + S - 1) // S * 512
+
+    budget = max(staged(sizes[r]) for r in small) + min(staged(sizes[r]) for r in small) - 1
+    assert staged(sizes[big]) > budget
     srv = bcd.Server(dg, max_device_bytes=budget)
     try:
         tb = srv.submit({"r": big, "kind": bcd.BC_QUERY_EXACT})
