@@ -208,6 +208,7 @@ typedef struct {
                                  shortest s-t path (the terms of the vertex scan) */
     double ms_root;           /* accumulation 2: CUDA-event time of the traversal from the
                                  query vertex (inside ms_spd, not in ms_traversal) */
+    int64_t pull_levels;      /* forward levels run bottom-up (bc_config.pull_permille) */
 } bc_batch_info;
 
 /*
@@ -356,6 +357,15 @@ void bc_server_destroy(bc_server *srv);
  *                  graphs. Results equal those of 1 up to fp64 rounding
  *                  order. On the R-MAT graphs of the benchmark a one-query
  *                  call runs about 1.4x faster.
+ *   pull_permille  direction of each forward level of the unweighted kernel:
+ *                  a level whose frontier's out-arcs number at least
+ *                  pull_permille / 1000 of the graph's arcs runs bottom-up
+ *                  (every vertex not yet reached by some source of the tile
+ *                  scans its in-arcs in R(G) and sums sigma over the
+ *                  in-neighbours on the current level, with no atomic per
+ *                  arc), the others top-down (the frontier pushes sigma
+ *                  along its out-arcs); 1..1000, or -1 for top-down only.
+ *                  Results are identical either way (sigma sums integers).
  *   timeout_us     limit, in microseconds of wall time, on every wait of a
  *                  traversal kernel at a grid-wide barrier (default
  *                  10,000,000: 10 s). A wait that runs out makes every block
@@ -372,6 +382,7 @@ typedef struct {
     int32_t weighted_words;
     int32_t accumulation;
     int32_t timeout_us;
+    int32_t pull_permille;
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);

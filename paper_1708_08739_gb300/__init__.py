@@ -71,13 +71,14 @@ class bc_batch_info(C.Structure):
                 ("ms_backward", C.c_double), ("tiles", C.c_int64), ("max_level", C.c_int32),
                 ("grid_blocks", C.c_int32), ("ms_traversal", C.c_double), ("reached_pairs", C.c_int64),
                 ("tight_pairs", C.c_int64), ("arc_visits", C.c_int64), ("union_vertices", C.c_int64),
-                ("union_arcs", C.c_int64), ("scan_pairs", C.c_int64), ("ms_root", C.c_double)]
+                ("union_arcs", C.c_int64), ("scan_pairs", C.c_int64), ("ms_root", C.c_double),
+                ("pull_levels", C.c_int64)]
 
 
 class bc_config(C.Structure):
     _fields_ = [("tile_words", C.c_int32), ("chunk_arcs", C.c_int32), ("block_threads", C.c_int32),
                 ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("weighted_words", C.c_int32),
-                ("accumulation", C.c_int32), ("timeout_us", C.c_int32)]
+                ("accumulation", C.c_int32), ("timeout_us", C.c_int32), ("pull_permille", C.c_int32)]
 
 
 class bc_server_config(C.Structure):
@@ -228,9 +229,9 @@ def bc_set_stream(g: Graph, stream):
 
 
 def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0,
-                  weighted_words=0, accumulation=0, timeout_us=0):
+                  weighted_words=0, accumulation=0, timeout_us=0, pull_permille=0):
     c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm),
-                  int(weighted_words), int(accumulation), int(timeout_us))
+                  int(weighted_words), int(accumulation), int(timeout_us), int(pull_permille))
     _check(lib().bc_set_config(g.handle, C.byref(c)))
 
 

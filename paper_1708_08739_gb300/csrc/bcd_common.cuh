@@ -42,6 +42,7 @@ struct Counters {
     unsigned long long vb;         // sum over tiles of distinct vertices reached
     unsigned long long eb;         // sum over tiles of the out-arcs of those vertices
     unsigned long long vpairs;     // vertex scan: (t, s) pairs with the query vertex on a shortest s-t path
+    unsigned long long pull_levels; // forward levels run bottom-up (pull over R(G))
 };
 
 // One unit of expansion work: arcs [a0, a0 + na) of vertex v, the k-th of
@@ -104,6 +105,12 @@ struct TravParams {
     int64_t *lev_icstart;          // [maxlev + 2] first in-arc chunk of each level
     int32_t maxlev;
     int32_t pad1;
+    // bottom-up forward levels: every vertex's in-arcs (R(G)) in chunks of
+    // chunk_arcs, as (vertex, chunk index) pairs, and the switch: a level runs
+    // bottom-up when its frontier's out-arcs reach pull_arcs_min (0: never)
+    const int2 *pchunks;
+    int64_t npchunks;
+    int64_t pull_arcs_min;
     // tiles
     const int32_t *srcs;  // [ntiles * S], -1 pads the last tile
     int64_t ntiles;
@@ -175,11 +182,15 @@ struct bcd_workspace {
     int64_t pcap = 0;
     unsigned long long *lev_cnt = nullptr;
     unsigned long long *lev_ccnt = nullptr;
-    unsigned long long *lev_grab = nullptr;
+    unsigned long long *lev_grab = nullptr;  // [6 * (maxlev + 2)]: forward and backward hand-out, in-arc chunk
+                                             // counts, frontier out-arc sums
     int64_t *lev_start = nullptr;
     int64_t *lev_cstart = nullptr;
     int64_t *lev_icstart = nullptr;
     int32_t maxlev = 0;
+    int2 *pchunks = nullptr;      // in-arc chunks of every vertex (bottom-up levels), unweighted graphs
+    int64_t npchunks = 0;
+    int32_t pchunk_arcs = 0;      // chunk_arcs the list was cut with
     // per-group state
     uint64_t *rvmask = nullptr;   // [n]
     uint64_t *need = nullptr;     // [n]
@@ -257,6 +268,7 @@ struct bc_graph {
     int blocks_per_sm = 1;        // resident blocks per SM of the 256-source kernel (1 or 2)
     int block_threads = 512;
     int accumulation = 2;         // 1: Eq. 4 push, 2: vertex scan for launches with one query vertex
+    int pull_permille = 0;        // bottom-up levels: frontier out-arcs >= pull_permille / 1000 of m (0: never)
     bcd_workspace ws;
     int64_t launches = 0;
     int last_grid = 0;                       // blocks of the last traversal launch
@@ -295,6 +307,7 @@ bc_status alloc_levels(bc_graph *g, int64_t maxlev);
 bc_status grow_levels(bc_graph *g);
 bc_status grow_buckets(bc_graph *g);
 int tile_words_of(const bc_graph *g);  // mask words of the tiles the graph's kernel runs
+bc_status ensure_pull_chunks(bc_graph *g);
 void free_workspace(bc_graph *g);
 
 // traversal launcher (bcd_traverse.cu)

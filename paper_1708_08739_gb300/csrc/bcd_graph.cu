@@ -169,6 +169,9 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->accumulation && c->accumulation != 1 && c->accumulation != 2)
         return set_error(BC_E_INVALID_ARG, "bc_set_config: accumulation must be 1 or 2");
     if (c->timeout_us < 0) return set_error(BC_E_INVALID_ARG, "bc_set_config: timeout_us must be positive (0 keeps it)");
+    if (c->pull_permille && (c->pull_permille < -1 || c->pull_permille > 1000))
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: pull_permille must be 1..1000 or -1 (0 keeps it)");
+    if (c->pull_permille) g->pull_permille = c->pull_permille < 0 ? 0 : c->pull_permille;
     if (c->timeout_us) g->timeout_ns = 1000.0 * (double)c->timeout_us;
     if (c->accumulation) g->accumulation = c->accumulation;
     if (c->tile_words) g->tile_words = c->tile_words;
@@ -187,6 +190,7 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->weighted_words = g->weighted_words;
     c->accumulation = g->accumulation;
     c->timeout_us = (int32_t)(g->timeout_ns / 1000.0);
+    c->pull_permille = g->pull_permille > 0 ? g->pull_permille : -1;
     return BC_OK;
 }
 

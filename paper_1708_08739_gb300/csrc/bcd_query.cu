@@ -294,6 +294,33 @@ bc_status grow_history(bc_graph *g) {
 
 int tile_words_of(const bc_graph *g) { return g->weighted ? g->weighted_words : g->tile_words; }
 
+// The in-arcs (R(G)) of every vertex with in-degree > 0, cut into chunks of
+// chunk_arcs arcs, as (vertex, chunk index) pairs: the work list of the
+// bottom-up forward levels. Built once per graph and chunk size.
+bc_status ensure_pull_chunks(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    const int CH = g->chunk_arcs;
+    if (ws.pchunks && ws.pchunk_arcs == CH) return BC_OK;
+    dev_free(ws.pchunks);
+    ws.npchunks = 0;
+    std::vector<int2> list;
+    list.reserve((size_t)g->n + (size_t)(g->m / CH) + 1);
+    for (int32_t v = 0; v < g->n; ++v) {
+        const int64_t d = g->h_roff[v + 1] - g->h_roff[v];
+        for (int64_t k = 0; k * CH < d; ++k) list.push_back(make_int2(v, (int)k));
+    }
+    const bc_status st = dev_alloc(&ws.pchunks, std::max<size_t>(list.size(), 1));
+    if (st != BC_OK) {
+        free_workspace(g);
+        return st;
+    }
+    if (!list.empty())
+        BCD_CUDA(cudaMemcpy(ws.pchunks, list.data(), sizeof(int2) * list.size(), cudaMemcpyHostToDevice));
+    ws.npchunks = (int64_t)list.size();
+    ws.pchunk_arcs = CH;
+    return BC_OK;
+}
+
 void free_workspace(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     dev_free(ws.vs);
@@ -313,6 +340,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.lev_start);
     dev_free(ws.lev_cstart);
     dev_free(ws.lev_icstart);
+    dev_free(ws.pchunks);
     dev_free(ws.rvmask);
     dev_free(ws.need);
     dev_free(ws.qmask);
@@ -1107,6 +1135,7 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.union_vertices += (int64_t)t.c.vb;
         bi.union_arcs += (int64_t)t.c.eb;
         bi.scan_pairs += (int64_t)t.c.vpairs;
+        bi.pull_levels += (int64_t)t.c.pull_levels;
         bi.ms_root += t.root;
         group.clear();
         return BC_OK;

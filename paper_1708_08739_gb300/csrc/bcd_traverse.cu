@@ -33,6 +33,8 @@
 // Counters::err and all blocks leave.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "bcd_common.cuh"
 #include "bcd_device.cuh"
 
@@ -66,12 +68,18 @@ __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app
     }
     const int tot = __shfl_sync(kFull, x, 31);
     const int toti = __shfl_sync(kFull, xi, 31);
+    // out-arcs of the appended vertices: the next level's frontier arcs, which
+    // choose its direction
+    unsigned long long fa = app ? (unsigned long long)(wre - wrb) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fa += __shfl_xor_sync(kFull, fa, o);
     unsigned long long eb = 0, cb = 0, ib = 0;
     if (lane == 0) {
         eb = atomicAdd(&p.lev_cnt[L + 1], (unsigned long long)ne);
         cb = atomicAdd(&p.lev_ccnt[L + 1], (unsigned long long)tot);
         if (MODE == kModeSpd && toti)
             ib = atomicAdd(&p.lev_grab[2 * ((long long)p.maxlev + 2) + L + 1], (unsigned long long)toti);
+        if (MODE != kModeReach && fa) atomicAdd(&p.lev_grab[3 * ((long long)p.maxlev + 2) + L + 1], fa);
     }
     eb = __shfl_sync(kFull, eb, 0);
     cb = __shfl_sync(kFull, cb, 0);
@@ -339,6 +347,197 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
     }
 }
 
+// Bottom-up step of level L (the forward pass of Section 2 read from the
+// other end): sigma_s(v) is the sum of sigma_s(u) over the in-neighbours u
+// of v at level L for s, so every vertex v that some source of the tile has
+// not reached yet (U = valid & ~(visited(v) | current(v))) scans its in-arcs
+// in R(G), and for each in-neighbour u the sources of current(u) & U reach v
+// at level L + 1, each adding sigma_s(u). The sums stay in registers: a
+// vertex whose in-arcs fit one chunk writes its sigma row and its next-level
+// mask once, with no atomic per arc (longer rows are cut into chunks that
+// meet in fp64 atomic adds, exact for integers below 2^53). Lane l holds
+// sources l + 32 i, as in the push. The level-L entries themselves get the
+// bookkeeping the push does for the first chunk of an entry: masks into the
+// history, visited |= F, work counters, query levels and the 2^53 check.
+// Appends are gathered in a per-warp buffer (lane i holds the i-th) and go
+// out 32 at a time through warp_append.
+template <int W, int MODE>
+__device__ __noinline__ void pull_level(const TravParams &p, int L, long long es, long long es1, long long cs1, long long ics1,
+                           Stats &st, const uint64_t *s_need, const uint64_t *s_valid, long long gwarp,
+                           long long nwarps) {
+    constexpr int S = 64 * W;
+    constexpr int PL = 2 * W;
+    const int lane = threadIdx.x & 31;
+    const int cur = 1 + (L & 1);
+    const int nxt = 1 + ((L + 1) & 1);
+    const int stride = p.vs_stride;
+    const int CH = p.chunk_arcs;
+    // (1) the level-L entries, one warp each
+    for (long long e = es + gwarp; e < es1; e += nwarps) {
+        const int v = p.hv[e];
+        const uint64_t *vrow = p.vs + (size_t)v * stride;
+        uint64_t F[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w) {
+                p.hm[(size_t)e * W + w] = F[w];
+                atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + w], (unsigned long long)F[w]);
+            }
+        if (lane == 0) {
+            int pc = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
+            st.edges += (unsigned)pc * (unsigned)(p.off[v + 1] - p.off[v]);
+            st.reached += (unsigned)pc;
+        }
+        const uint64_t qm = p.qmask[v];
+        const double *srow = p.sigma + (size_t)v * S;
+#pragma unroll
+        for (int ii = 0; ii < PL; ++ii) {
+            const int s = lane + 32 * ii;
+            if (mask_bit<W>(F, s)) {
+                if (qm) {
+                    uint64_t x = qm & s_need[s];
+                    while (x) {
+                        const int q = __ffsll((long long)x) - 1;
+                        x &= x - 1;
+                        p.qlevel[s * 64 + q] = L;
+                    }
+                }
+                if (srow[s] >= 9007199254740992.0)
+                    atomicOr((unsigned long long *)&p.srcflag[s >> 6], 1ull << (s & 63));
+            }
+        }
+    }
+    // (2) every vertex's in-arc chunks, handed out dynamically
+    int bv = 0, bnch = 0, binch = 0, bcnt = 0;
+    long long brb = 0, bre = 0, birb = 0, bire = 0;
+    ChunkGrabber grab(&p.lev_grab[L], p.npchunks, nwarps);
+    long long c;
+    while (grab.next(c, lane)) {
+        const int2 pc = p.pchunks[c];
+        const int v = pc.x;
+        const uint64_t *vrow = p.vs + (size_t)v * stride;
+        uint64_t U[W];
+        bool anyu = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            U[w] = s_valid[w] & ~(vrow[w] | vrow[cur * W + w]);
+            anyu |= U[w] != 0ull;
+        }
+        if (!anyu) continue;  // every source of the tile has reached v
+        const long long rb = p.roff[v], re = p.roff[v + 1];
+        const long long a0 = rb + (long long)pc.y * CH;
+        const int na = (int)min((long long)CH, re - a0);
+        const int nch = (int)((re - rb + CH - 1) / CH);
+        double acc[PL];
+#pragma unroll
+        for (int ii = 0; ii < PL; ++ii) acc[ii] = 0.0;
+        unsigned lm = 0;  // bit ii: source lane + 32 ii reaches v here
+        int unext = lane < na ? p.rcol[a0 + lane] : 0;
+        for (int base = 0; base < na; base += 32) {
+            const bool valid = base + lane < na;
+            const int u = unext;
+            unext = base + 32 + lane < na ? p.rcol[a0 + base + 32 + lane] : 0;
+            uint64_t t[W];
+            bool any = false;
+            if (valid) {
+                const uint64_t *urow = p.vs + (size_t)u * stride;
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    t[w] = urow[cur * W + w] & U[w];
+                    any |= t[w] != 0ull;
+                }
+                st.arcs += 1;
+#pragma unroll
+                for (int w = 0; w < W; ++w) st.tight += (unsigned)__popcll(t[w]);
+            } else {
+#pragma unroll
+                for (int w = 0; w < W; ++w) t[w] = 0ull;
+            }
+            // two tight in-neighbours per step: their gathers overlap
+            unsigned bal = __ballot_sync(kFull, any);
+            while (bal) {
+                const int i0 = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int i1 = bal ? __ffs(bal) - 1 : -1;
+                if (bal) bal &= bal - 1;
+                const int j1 = i1 < 0 ? i0 : i1;
+                const int u0 = __shfl_sync(kFull, u, i0);
+                const int u1 = __shfl_sync(kFull, u, j1);
+                uint64_t n0[W], n1[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    n0[w] = __shfl_sync(kFull, t[w], i0);
+                    n1[w] = i1 < 0 ? 0ull : __shfl_sync(kFull, t[w], j1);
+                }
+                const double *r0 = p.sigma + (size_t)u0 * S;
+                const double *r1 = p.sigma + (size_t)u1 * S;
+#pragma unroll
+                for (int ii = 0; ii < PL; ++ii) {
+                    const int s = lane + 32 * ii;
+                    const bool b0 = mask_bit<W>(n0, s), b1 = mask_bit<W>(n1, s);
+                    const double x0 = b0 ? r0[s] : 0.0;
+                    const double x1 = b1 ? r1[s] : 0.0;
+                    acc[ii] += x0 + x1;
+                    if (b0 | b1) lm |= 1u << ii;
+                }
+            }
+        }
+        uint64_t nm[W];
+        bool anynm = false;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const unsigned lo = __ballot_sync(kFull, (lm >> (2 * w)) & 1u);
+            const unsigned hi = __ballot_sync(kFull, (lm >> (2 * w + 1)) & 1u);
+            nm[w] = (uint64_t)lo | ((uint64_t)hi << 32);
+            anynm |= nm[w] != 0ull;
+        }
+        if (!anynm) continue;
+        // the next-level mask (atomic: the stale level L - 1 bits of this slot
+        // are being cleared at the same time) and sigma
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w && nm[w])
+                atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + nxt * W + w], (unsigned long long)nm[w]);
+        double *srow = p.sigma + (size_t)v * S;
+#pragma unroll
+        for (int ii = 0; ii < PL; ++ii)
+            if ((lm >> ii) & 1u) {
+                if (nch == 1)
+                    srow[lane + 32 * ii] = acc[ii];
+                else
+                    atomicAdd(&srow[lane + 32 * ii], acc[ii]);
+            }
+        int old = 0;
+        if (lane == 0) old = atomicMax(&p.tag[v], L + 1);
+        old = __shfl_sync(kFull, old, 0);
+        if (old < L + 1) {
+            const long long wrb = p.off[v], wre = p.off[v + 1];
+            if (lane == 0 && old < 0) {
+                st.vb += 1;
+                st.eb += (unsigned)(wre - wrb);
+            }
+            if (lane == bcnt) {
+                bv = v;
+                brb = wrb;
+                bre = wre;
+                bnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
+                birb = rb;
+                bire = re;
+                binch = MODE == kModeSpd ? nch : 0;
+            }
+            if (++bcnt == 32) {
+                warp_append<W, MODE>(p, L, true, bv, bnch, brb, bre, binch, birb, bire, es1, cs1, ics1, lane);
+                bcnt = 0;
+            }
+        }
+    }
+    warp_append<W, MODE>(p, L, lane < bcnt, bv, bnch, brb, bre, binch, birb, bire, es1, cs1, ics1, lane);
+}
+
 // Eq. 4, push form, from level L into level L - 1: each entry w of level L
 // sends c_s(w) = (1 + delta_s(w)) / sigma_s(w), with delta_s(w) =
 // sigma_s(w) * acc_s(w) complete (level L + 1 pushed into it in the previous
@@ -587,6 +786,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
     __shared__ int32_t s_minql[S];
     __shared__ uint64_t s_active[W];
     __shared__ uint64_t s_active_next[W];
+    __shared__ uint64_t s_valid[W];  // the tile's occupied source slots
     __shared__ int32_t s_lstop;
     Stats st;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -600,6 +800,12 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
             s_need[s] = (MODE != kModeReach && v >= 0) ? p.need[v] : 0ull;
+        }
+        if (threadIdx.x < W) {
+            uint64_t m = 0;
+            for (int b = 0; b < 64; ++b)
+                if (tsrc[threadIdx.x * 64 + b] >= 0) m |= 1ull << b;
+            s_valid[threadIdx.x] = m;
         }
         if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
         if (timer) {
@@ -635,7 +841,16 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                         atomicAnd((unsigned long long *)&row[nxt * W + w], ~(unsigned long long)p.hm[e * W + w]);
                 }
             }
-            forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, ics1, st, s_need, gwarp, nwarps);
+            // direction of level L: bottom-up when its frontier's out-arcs
+            // reach the threshold (the same counter in every block)
+            const bool pull = MODE != kModeReach && L >= 1 && p.pull_arcs_min > 0 &&
+                              (long long)ld_vol(&p.lev_grab[3 * ((long long)p.maxlev + 2) + L]) >= p.pull_arcs_min;
+            if (pull) {
+                pull_level<W, MODE>(p, L, es, es1, cs1, ics1, st, s_need, s_valid, gwarp, nwarps);
+                if (timer) atomicAdd(&p.ctr->pull_levels, 1ull);
+            } else {
+                forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, ics1, st, s_need, gwarp, nwarps);
+            }
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             total = es1;
             if (ld_vol(&p.lev_cnt[L + 1]) == 0ull) break;
@@ -787,6 +1002,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                     p.lev_grab[l] = 0ull;
                     p.lev_grab[p.maxlev + 2 + l] = 0ull;
                     p.lev_grab[2 * (p.maxlev + 2) + l] = 0ull;
+                    p.lev_grab[3 * (p.maxlev + 2) + l] = 0ull;
                 }
             }
         }
@@ -873,6 +1089,13 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         p.chunk_arcs = g->chunk_arcs;
         p.timeout_ns = g->timeout_ns;
         p.cancel = g->cancel_d;
+        p.pull_arcs_min = 0;
+        if (!g->weighted && p.mode != kModeReach && g->pull_permille > 0) {
+            BCD_TRY(ensure_pull_chunks(g));
+            p.pchunks = ws.pchunks;
+            p.npchunks = ws.npchunks;
+            p.pull_arcs_min = std::max<int64_t>(1, (int64_t)((double)g->m * g->pull_permille / 1000.0));
+        }
         BCD_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), g->stream));
         bc_status st = BC_E_INTERNAL;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;

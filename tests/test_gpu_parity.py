@@ -421,3 +421,64 @@ def test_batch_shards_add_up(bcd, er1, nshards):
             assert out[i]["samples"] == outs[0][i]["samples"]
     with pytest.raises(bcd.BCError):
         bcd.bc_batch_shard(dg, specs, nshards, nshards)
+
+
+# ---------------------------------------------------------------- bottom-up levels
+
+@pytest.mark.parametrize("cfg", [{"pull_permille": 1}, {"pull_permille": 1, "tile_words": 1},
+                                 {"pull_permille": 1, "tile_words": 2, "chunk_arcs": 32},
+                                 {"pull_permille": 50}])
+def test_bottom_up_levels_bit_exact(bcd, er1, cfg):
+    """Forward levels run bottom-up (every level from 1 on with 1 permille):
+    distances and sigma stay bit-exact, dependencies and scores within the
+    bar, in both accumulations."""
+    g, og = er1
+    dg = make(bcd, g, **cfg)
+    srcs = np.array(sorted(set(gg.random_vertices(g.n, 40, 7).tolist())), dtype=np.int32)[:37]
+    tgts = np.array(list(dict.fromkeys(gg.random_vertices(g.n, 20, 8).tolist())), dtype=np.int32)
+    dist, sig, dep, flags = bcd.bc_spd_probe(dg, srcs, tgts)
+    for i, s in enumerate(srcs.tolist()):
+        st = O.source_state(og, s)
+        assert np.array_equal(dist[i], st["dist"]), s
+        assert np.array_equal(sig[i], st["sigma"]), s
+        for j, t in enumerate(tgts.tolist()):
+            if t != s:
+                assert close(dep[i, j], st["delta"][t]), (s, t, dep[i, j], st["delta"][t])
+    qs = gg.random_vertices(g.n, 10, 102).tolist()
+    out, info = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    assert info["pull_levels"] > 0
+    for r, o in zip(qs, out):
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), r
+    bcd.bc_set_config(dg, accumulation=2)
+    got, _ = bcd.bc_exact(dg, qs[0])
+    assert close(got, O.bc_exact(og, qs[0], 0)[0])
+
+
+def test_bottom_up_heavy_rows(bcd):
+    """A hub with 20,000 in-arcs: its in-arc row is cut into chunks whose
+    sigma sums meet in atomic adds; path counts on a diamond chain reach
+    2^52 through bottom-up levels."""
+    n = 20001
+    arcs = [(0, i) for i in range(1, n)] + [(i, 0) for i in range(1, n)]
+    arcs += [(i, i + 1) for i in range(1, n - 1)]
+    g = csr(n, arcs)
+    og = O.Graph.from_csr(g)
+    for cfg in [{"pull_permille": 1}, {"pull_permille": 1, "chunk_arcs": 32}]:
+        dg = make(bcd, g, **cfg)
+        for r in [0, 5, 19999]:
+            assert close(bcd.bc_exact(dg, r)[0], O.bc_exact(og, r, 0)[0]), (cfg, r)
+        dist, sig, _, _ = bcd.bc_spd_probe(dg, [3, 0, 700], [0])
+        for i, s in enumerate([3, 0, 700]):
+            st = O.source_state(og, s)
+            assert np.array_equal(dist[i], st["dist"]) and np.array_equal(sig[i], st["sigma"]), (cfg, s)
+    k = 52
+    arcs = []
+    for i in range(k):
+        a, b, c, d = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        arcs += [(a, b), (a, c), (b, d), (c, d)]
+    g = csr(3 * k + 1, arcs)
+    og = O.Graph.from_csr(g)
+    dg = make(bcd, g, pull_permille=1)
+    dist, sig, _, flags = bcd.bc_spd_probe(dg, [0], [3 * k])
+    st = O.source_state(og, 0)
+    assert np.array_equal(sig[0], st["sigma"]) and sig[0, 3 * k] == 2.0 ** k and flags[0] == 0
