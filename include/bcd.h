@@ -209,6 +209,7 @@ typedef struct {
     double ms_root;           /* accumulation 2: CUDA-event time of the traversal from the
                                  query vertex (inside ms_spd, not in ms_traversal) */
     int64_t pull_levels;      /* forward levels run bottom-up (bc_config.pull_permille) */
+    int64_t scan_tiles;       /* tiles whose dependencies came from the vertex scan */
 } bc_batch_info;
 
 /*
@@ -342,21 +343,35 @@ void bc_server_destroy(bc_server *srv);
  *                  1 the backward pass of Eq. 4, deepest level first
  *                  (unweighted: pushed along the tight in-arcs of R(G);
  *                  weighted: pulled over the tight out-arcs);
- *                  2 (default) a vertex scan, used when every query of a
- *                  call (or of a bc_batch group) has the same vertex r,
- *                  else 1 (groups with several vertices, serving): one
+ *                  2 a vertex scan when every query of a call (or of a
+ *                  bc_batch group) has the same vertex r, else 1: one
  *                  forward traversal from r gives d(r,t) and sigma_rt, and
  *                  after each tile's forward pass
  *                    delta_s.(r) = sigma_sr * sum over t != s, r with
  *                                  d(s,r) + d(r,t) = d(s,t) of sigma_rt / sigma_st
  *                  (Eq. 2 summed over the pair dependencies, with
  *                  sigma_st(r) = sigma_sr * sigma_rt when r lies on a
- *                  shortest s-t path: the Bellman criterion),
- *                  one pass over the tile's reached (vertex, source) pairs
- *                  with no per-level barrier, on unweighted and weighted
- *                  graphs. Results equal those of 1 up to fp64 rounding
- *                  order. On the R-MAT graphs of the benchmark a one-query
- *                  call runs about 1.4x faster.
+ *                  shortest s-t path: the Bellman criterion), one pass over
+ *                  the tile's reached (vertex, source) pairs with no
+ *                  per-level barrier, on unweighted and weighted graphs;
+ *                  3 the vertex scan for every group of an unweighted graph,
+ *                  with its queries at up to 64 distinct vertices r_c: one
+ *                  traversal rooted at all of them gives d(r_c, t) and
+ *                  sigma_{r_c t} (12 bytes per vertex and column, 64 columns
+ *                  allocated on first use), and each tile's pass screens its
+ *                  reached (vertex, source) pairs for 8 columns at a time;
+ *                  weighted graphs keep 2's choice;
+ *                  4 (default) 2 for one-vertex groups and, for a group
+ *                  at several vertices of an unweighted graph, 3 on its
+ *                  first tile, then for the remaining tiles the scan when
+ *                  its terms on that tile, weighted 16 to 1, did not
+ *                  outnumber the tight (source, arc) pairs the Eq. 4 push
+ *                  would add, else 1. The scan wins where few shortest
+ *                  paths run through the query vertices (1.5x on the
+ *                  benchmark's R-MAT 22 batch of 64 uniform vertices) and
+ *                  loses on hubs (4-5x slower for the 32 vertices of
+ *                  largest in-degree x out-degree of R-MAT 20).
+ *                  Results equal those of 1 up to fp64 rounding order.
  *   pull_permille  direction of each forward level of the unweighted kernel:
  *                  a level whose frontier's out-arcs number at least
  *                  pull_permille / 1000 of the graph's arcs runs bottom-up

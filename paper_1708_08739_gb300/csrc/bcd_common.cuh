@@ -144,6 +144,17 @@ struct TravParams {
                              // sigma_rt / sigma_st; weighted: sum_t sigma_rt / sigma_st, then sigma_sr)
     int32_t vroot;
     int32_t pad2;
+    // vertex scan over several query vertices (columns): column c of the
+    // group's distinct query vertices croot[c]; query bit q belongs to column
+    // qcol[q]; rlevq / rsigq [t * 64 + c] = d(croot[c], t) and sigma from it;
+    // msum [s * 64 + c] the per-(source, column) sums of the current tile
+    int32_t ncols;           // 0 or 1: the one-vertex scan above
+    int32_t pad3;
+    const int32_t *qcol;     // [64]
+    const int32_t *croot;    // [64]
+    int32_t *rlevq;          // [n * 64], -1 unreached
+    double *rsigq;           // [n * 64]
+    double *msum;            // [S * 64]
     // reach mode output
     uint64_t *rvmask;        // [n]
     int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
@@ -212,6 +223,9 @@ struct bcd_workspace {
     uint64_t *rdist = nullptr;    // [n] ... distances from it (weighted graphs)
     double *rsig = nullptr;       // [n] ... and its path counts
     double *vsum = nullptr;       // [2 * 64 * W] ... and the per-source sums of a tile
+    int32_t *rlevq = nullptr;     // [n * 64] several query vertices: levels from each (unweighted graphs)
+    double *rsigq = nullptr;      // [n * 64] ... and path counts
+    double *msum = nullptr;       // [64 * W * 64] per-(source, column) sums of a tile
     int32_t *rtile = nullptr;     // [64 * W] the one-source tile of the query vertex's traversal
     uint32_t *qflags = nullptr;   // [64]
     uint64_t *srcflag = nullptr;  // [W]
@@ -267,7 +281,7 @@ struct bc_graph {
     int source_order = 1;         // 1: tiles ordered by distance to the hub, 0: by vertex id
     int blocks_per_sm = 1;        // resident blocks per SM of the 256-source kernel (1 or 2)
     int block_threads = 512;
-    int accumulation = 2;         // 1: Eq. 4 push, 2: vertex scan for launches with one query vertex
+    int accumulation = 4;         // 1: Eq. 4 push, 2: vertex scan for one-vertex groups, 3: scan always, 4: chosen per group
     int pull_permille = 0;        // bottom-up levels: frontier out-arcs >= pull_permille / 1000 of m (0: never)
     bcd_workspace ws;
     int64_t launches = 0;

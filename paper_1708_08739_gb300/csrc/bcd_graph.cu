@@ -166,8 +166,8 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
         if (!g->weighted && bt < 64 * tw)
             return set_error(BC_E_INVALID_ARG, "bc_set_config: block_threads must be at least 64 * tile_words");
     }
-    if (c->accumulation && c->accumulation != 1 && c->accumulation != 2)
-        return set_error(BC_E_INVALID_ARG, "bc_set_config: accumulation must be 1 or 2");
+    if (c->accumulation && (c->accumulation < 1 || c->accumulation > 4))
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: accumulation must be 1, 2, 3 or 4");
     if (c->timeout_us < 0) return set_error(BC_E_INVALID_ARG, "bc_set_config: timeout_us must be positive (0 keeps it)");
     if (c->pull_permille && (c->pull_permille < -1 || c->pull_permille > 1000))
         return set_error(BC_E_INVALID_ARG, "bc_set_config: pull_permille must be 1..1000 or -1 (0 keeps it)");

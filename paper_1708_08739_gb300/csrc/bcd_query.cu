@@ -357,6 +357,9 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.rdist);
     dev_free(ws.rsig);
     dev_free(ws.vsum);
+    dev_free(ws.rlevq);
+    dev_free(ws.rsigq);
+    dev_free(ws.msum);
     dev_free(ws.rtile);
     dev_free(ws.qflags);
     dev_free(ws.srcflag);
@@ -418,6 +421,7 @@ static bc_status build_workspace(bc_graph *g, int W) {
         BCD_TRY(dev_alloc(&ws.rlev, (size_t)n));
     BCD_TRY(dev_alloc(&ws.rsig, (size_t)n));
     BCD_TRY(dev_alloc(&ws.vsum, (size_t)2 * 64 * W));
+    BCD_TRY(dev_alloc(&ws.msum, (size_t)64 * W * 64));
     BCD_TRY(dev_alloc(&ws.rtile, (size_t)64 * W));
     BCD_TRY(dev_alloc(&ws.qflags, 64));
     BCD_TRY(dev_alloc(&ws.srcflag, (size_t)std::max(W, 4)));
@@ -468,6 +472,7 @@ struct GroupTimes {
     bcd::Counters c{};
     int64_t sources = 0;
     int64_t tiles = 0;
+    int64_t scan_tiles = 0;  // tiles whose dependencies came from the vertex scan
     unsigned long long edges = 0;
     int levels = 0;
 };
@@ -693,7 +698,76 @@ static bc_status root_traversal(bc_graph *g, int32_t r) {
     return run_traversal(g, W, p, nullptr, nullptr);
 }
 
-static bool use_vertex_scan(const bc_graph *g, size_t nroots) { return g->accumulation == 2 && nroots == 1; }
+// The vertex scan replaces the Eq. 4 backward for groups whose queries sit at
+// one vertex (accumulation 2, the default) or, on unweighted graphs, at up to
+// 64 vertices (accumulation 3).
+static bool use_vertex_scan(const bc_graph *g, size_t nroots) {
+    if (nroots == 1) return g->accumulation >= 2;
+    return g->accumulation >= 3 && !g->weighted && nroots <= 64;
+}
+
+// Cost of one term of the vertex scan (a division and a shared-memory add,
+// with the lanes of a warp on one pair's sources) in units of one tight
+// (source, arc) pair of the Eq. 4 push (an fp64 reduction). Measured on the
+// R-MAT benchmark graphs: 13-20.
+constexpr unsigned long long kScanPairCost = 16;
+
+// Offsets in bcd_workspace::small of the column tables of a multi-vertex scan.
+constexpr int kSmallQcol = 1024;   // 64 int32: column of each query bit
+constexpr int kSmallCroot = 1056;  // 64 int32: vertex of each column
+static_assert(kSmallSpecs + 64 * 6 <= kSmallQcol && kSmallCroot + 32 <= kSmallWords, "small table layout");
+
+// d(r_c, t) and sigma_{r_c t} for every vertex t and each of several query
+// vertices r_c (the columns): one scan-mode launch over a tile whose slot c
+// holds r_c, kept in rlevq / rsigq [t * 64 + c].
+static bc_status root_traversal_multi(bc_graph *g, const std::vector<int32_t> &roots) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    const int W = tile_words_of(g);
+    const int S = 64 * W;
+    const int K = (int)roots.size();
+    if (!ws.rlevq) {
+        BCD_TRY(dev_alloc(&ws.rlevq, (size_t)g->n * 64));
+        bc_status st = dev_alloc(&ws.rsigq, (size_t)g->n * 64);
+        if (st != BC_OK) {
+            dev_free(ws.rlevq);
+            return st;
+        }
+    }
+    BCD_CUDA(cudaMemsetAsync(ws.rlevq, 0xff, sizeof(int32_t) * (size_t)g->n * 64, s));
+    std::vector<int32_t> tsrc(S, -1);
+    for (int c = 0; c < K; ++c) tsrc[c] = roots[c];
+    BCD_CUDA(cudaMemcpyAsync(ws.rtile, tsrc.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+    BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, 64));
+    TravParams p;
+    memset(&p, 0, sizeof(p));
+    p.mode = kModeScan;
+    p.flags = kFlagRootOut;
+    p.off = g->d_off;
+    p.col = g->d_col;
+    p.srcs = ws.rtile;
+    p.ntiles = 1;
+    p.qmask = ws.qmask;
+    p.need = ws.need;
+    p.exact_q = 0;
+    p.mult = nullptr;
+    p.qlevel = ws.qlevel;
+    p.dep = ws.dep;
+    p.tile_partial = ws.tile_partial;
+    p.qflags = ws.qflags;
+    p.srcflag = ws.srcflag;
+    p.rlev = ws.rlev;
+    p.rsig = ws.rsig;
+    p.vsum = ws.vsum;
+    p.ncols = K;
+    p.qcol = (const int32_t *)(ws.small + kSmallQcol);  // uploaded by the caller
+    p.croot = (const int32_t *)(ws.small + kSmallCroot);
+    p.rlevq = ws.rlevq;
+    p.rsigq = ws.rsigq;
+    p.msum = ws.msum;
+    p.vroot = roots[0];
+    return run_traversal(g, W, p, nullptr, nullptr);
+}
 
 // Tiles [lo, hi) of shard k out of nshards contiguous shards of ntiles tiles.
 static void shard_tiles(int64_t ntiles, int32_t k, int32_t nshards, int64_t *lo, int64_t *hi) {
@@ -839,41 +913,90 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     int levels = 0;
     unsigned long long edges = 0;
     const bool scan = nrun > 0 && use_vertex_scan(g, roots.size());
-    if (scan) {
+    const bool multi = scan && roots.size() >= 2;
+    if (multi) {
+        std::vector<int32_t> qcol(64, 0), croot(64, 0);
+        for (int i = 0; i < nq; ++i) qcol[i] = qs[i].slot;
+        for (size_t c = 0; c < roots.size(); ++c) croot[c] = roots[c];
+        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallQcol, qcol.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallCroot, croot.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        BCD_TRY(root_traversal_multi(g, roots));
+        tm.root = g->last_ms_launch;
+    } else if (scan) {
         BCD_TRY(root_traversal(g, roots[0]));
         tm.root = g->last_ms_launch;
     }
     if (nrun > 0) {
         BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, nrun * 64));
-        TravParams p;
-        memset(&p, 0, sizeof(p));
-        p.mode = scan ? kModeScan : kModeSpd;
-        p.flags = 0;
-        if (scan) {
-            p.rlev = ws.rlev;
-            p.rdist = ws.rdist;
-            p.rsig = ws.rsig;
-            p.vsum = ws.vsum;
-            p.vroot = roots[0];
+        // tiles [first, first + count) of this call's range, in scan or Eq. 4 mode
+        auto launch_tiles = [&](bool scan_mode, int64_t first, int64_t count) -> bc_status {
+            TravParams p;
+            memset(&p, 0, sizeof(p));
+            p.mode = scan_mode ? kModeScan : kModeSpd;
+            p.flags = 0;
+            if (scan_mode) {
+                p.rlev = ws.rlev;
+                p.rdist = ws.rdist;
+                p.rsig = ws.rsig;
+                p.vsum = ws.vsum;
+                p.vroot = roots[0];
+            }
+            if (scan_mode && multi) {
+                p.ncols = (int32_t)roots.size();
+                p.qcol = (const int32_t *)(ws.small + kSmallQcol);
+                p.croot = (const int32_t *)(ws.small + kSmallCroot);
+                p.rlevq = ws.rlevq;
+                p.rsigq = ws.rsigq;
+                p.msum = ws.msum;
+            }
+            p.off = g->d_off;
+            p.col = g->d_col;
+            p.srcs = ws.dlist + (t_lo + first) * S;
+            p.ntiles = count;
+            p.qmask = ws.qmask;
+            p.need = ws.need;
+            p.exact_q = exact_q;
+            p.mult = specs.empty() ? nullptr : ws.mult + (size_t)(t_lo + first) * S * 64;
+            p.qlevel = ws.qlevel;
+            p.dep = ws.dep;
+            p.tile_partial = ws.tile_partial + first * 64;
+            p.qflags = ws.qflags;
+            p.srcflag = ws.srcflag;
+            int lv = 0;
+            unsigned long long ed = 0;
+            BCD_TRY(run_traversal(g, W, p, &lv, &ed));
+            levels = std::max(levels, lv);
+            edges += ed;
+            tm.fwd += g->last_ns_fwd * 1e-6;
+            tm.bwd += g->last_ns_bwd * 1e-6;
+            tm.trav += g->last_ms_launch;
+            const Counters &c = g->last;
+            tm.c.reached += c.reached;
+            tm.c.tight += c.tight;
+            tm.c.arc_visits += c.arc_visits;
+            tm.c.vb += c.vb;
+            tm.c.eb += c.eb;
+            tm.c.vpairs += c.vpairs;
+            tm.c.pull_levels += c.pull_levels;
+            return BC_OK;
+        };
+        std::vector<uint32_t> cal_flags(64, 0);
+        if (multi && g->accumulation == 4 && nrun > 1) {
+            // choose the backward on the group's first tile: the scan's terms
+            // (a division and a shared-memory add each) against the push's
+            // tight (source, arc) pairs (an fp64 reduction each), at the
+            // measured cost ratio of about 16
+            BCD_TRY(launch_tiles(true, 0, 1));
+            BCD_CUDA(cudaMemcpyAsync(cal_flags.data(), ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            BCD_CUDA(cudaStreamSynchronize(s));
+            const bool scan_rest = g->last.vpairs * kScanPairCost <= g->last.tight;
+            tm.scan_tiles += 1;
+            BCD_TRY(launch_tiles(scan_rest, 1, nrun - 1));
+            if (scan_rest) tm.scan_tiles += nrun - 1;
+        } else {
+            BCD_TRY(launch_tiles(scan, 0, nrun));
+            if (scan) tm.scan_tiles += nrun;
         }
-        p.off = g->d_off;
-        p.col = g->d_col;
-        p.srcs = ws.dlist + t_lo * S;
-        p.ntiles = nrun;
-        p.qmask = ws.qmask;
-        p.need = ws.need;
-        p.exact_q = exact_q;
-        p.mult = specs.empty() ? nullptr : ws.mult + (size_t)t_lo * S * 64;
-        p.qlevel = ws.qlevel;
-        p.dep = ws.dep;
-        p.tile_partial = ws.tile_partial;
-        p.qflags = ws.qflags;
-        p.srcflag = ws.srcflag;
-        BCD_TRY(run_traversal(g, W, p, &levels, &edges));
-        tm.fwd = g->last_ns_fwd * 1e-6;
-        tm.bwd = g->last_ns_bwd * 1e-6;
-        tm.trav = g->last_ms_launch;
-        tm.c = g->last;
         std::vector<double> scale(64, 1.0);
         for (int i = 0; i < nq; ++i)
             if (qs[i].sampled && qs[i].rv > 0) scale[i] = (double)qs[i].rv / (double)qs[i].T;
@@ -883,6 +1006,8 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
         reduce_tiles<<<64, 256, 0, s>>>(ws.tile_partial, nrun, d_scale, d_out);
         BCD_CUDA(cudaMemcpyAsync(sums.data(), d_out, 64 * sizeof(double), cudaMemcpyDeviceToHost, s));
         BCD_CUDA(cudaMemcpyAsync(qflags.data(), ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        BCD_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < 64; ++i) qflags[i] |= cal_flags[i];
         g->launches += 1;
     }
     set_bits<<<1, 64, 0, s>>>(ws.qmask, d_qb, nq, 1);
@@ -1136,6 +1261,7 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.union_arcs += (int64_t)t.c.eb;
         bi.scan_pairs += (int64_t)t.c.vpairs;
         bi.pull_levels += (int64_t)t.c.pull_levels;
+        bi.scan_tiles += t.scan_tiles;
         bi.ms_root += t.root;
         group.clear();
         return BC_OK;

@@ -162,6 +162,8 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
         if (t < W) p.srcflag[t] = 0ull;
     }
     if (MODE == kModeScan && t < S) p.vsum[t] = 0.0;
+    if (MODE == kModeScan && p.ncols >= 2)
+        for (int i = t; i < S * 64; i += blockDim.x) p.msum[i] = 0.0;
     __syncthreads();
     if (t == 0) {
         p.lev_cnt[0] = (unsigned long long)s_valid;
@@ -772,6 +774,141 @@ __device__ void vertex_scan(const TravParams &p, int Lmax, const uint64_t *s_nee
     if (lane == 0 && pairs) atomicAdd(&p.ctr->vpairs, (unsigned long long)pairs);
 }
 
+// Dependencies on several query vertices at once by the vertex scan: the
+// form of vertex_scan for a group whose queries sit at up to 64 distinct
+// vertices (columns c, vertex croot[c]). rlevq / rsigq [t * 64 + c] hold
+// d(croot[c], t) and sigma_{croot[c] t} from one traversal rooted at all the
+// columns. Columns go 8 at a time (one 32-byte sector of a row of rlevq).
+// Each warp screens 32 level-L entries at a time: entry (t, F) is kept for
+// column c when L - d(r_c, t) is a level at which a source of the tile that
+// needs c meets r_c (the same screen as the one-vertex scan). For a kept
+// (entry, column), each lane adds sigma_{r_c t} / sigma_st, for its sources s
+// in F that need c and have d(s, r_c) = L - d(r_c, t), into the block's
+// shared sums [s][c]; at the end of the 8 columns the block multiplies them by
+// sigma_s(r_c) and adds them into msum [s * 64 + c] with one fp64 atomic each.
+// No level order and no grid barrier inside.
+template <int W>
+__device__ __noinline__ void vertex_scan_multi(const TravParams &p, int Lmax, const uint64_t *s_need, long long gwarp,
+                                               long long nwarps) {
+    constexpr int S = 64 * W;
+    constexpr int PL = 2 * W;
+    constexpr int G = 8;  // columns per pass
+    __shared__ double s_acc[S * G];
+    __shared__ int32_t s_ql[S * G];  // d(s, r_c) for sources that need column c, else -1
+    __shared__ int32_t s_kmin[G], s_kmax[G];
+    __shared__ unsigned long long s_kset[G];
+    const int lane = threadIdx.x & 31;
+    unsigned pairs = 0;
+    for (int cg = 0; cg < p.ncols; cg += G) {
+        const int nc = min(G, p.ncols - cg);
+        __syncthreads();
+        for (int i = threadIdx.x; i < S * G; i += blockDim.x) {
+            s_acc[i] = 0.0;
+            s_ql[i] = -1;
+        }
+        if (threadIdx.x < G) {
+            s_kmin[threadIdx.x] = 0x7fffffff;
+            s_kmax[threadIdx.x] = -1;
+            s_kset[threadIdx.x] = 0ull;
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < S; s += blockDim.x) {
+            uint64_t x = s_need[s];
+            while (x) {
+                const int q = __ffsll((long long)x) - 1;
+                x &= x - 1;
+                const int j = p.qcol[q] - cg;
+                if (j < 0 || j >= nc) continue;
+                const int lv = p.qlevel[s * 64 + q];
+                if (lv < 1) continue;
+                s_ql[s * G + j] = lv;
+                atomicMin(&s_kmin[j], lv);
+                atomicMax(&s_kmax[j], lv);
+                if (lv < 64) atomicOr(&s_kset[j], 1ull << lv);
+            }
+        }
+        __syncthreads();
+        int kmin[G], kmax[G];
+        unsigned long long kset[G];
+        int lfrom = 0x7fffffff;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            kmin[j] = s_kmin[j];
+            kmax[j] = s_kmax[j];
+            kset[j] = s_kset[j];
+            if (kmax[j] >= 1) lfrom = min(lfrom, kmin[j] + 1);
+        }
+        for (int L = lfrom; L <= Lmax; ++L) {
+            const long long eend = p.lev_start[L + 1];
+            for (long long b = p.lev_start[L] + 32 * gwarp; b < eend; b += 32 * nwarps) {
+                const long long e = b + lane;
+                int t = 0;
+                unsigned kq = 0;
+                int dr[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) dr[j] = -1;
+                if (e < eend) {
+                    t = p.hv[e];
+                    const int4 *row = reinterpret_cast<const int4 *>(p.rlevq + (size_t)t * 64 + cg);
+                    const int4 a = row[0], c = row[1];
+                    dr[0] = a.x; dr[1] = a.y; dr[2] = a.z; dr[3] = a.w;
+                    dr[4] = c.x; dr[5] = c.y; dr[6] = c.z; dr[7] = c.w;
+#pragma unroll
+                    for (int j = 0; j < G; ++j) {
+                        const int k = L - dr[j];
+                        if (j < nc && dr[j] >= 1 && k >= kmin[j] && k <= kmax[j] && (k >= 64 || ((kset[j] >> k) & 1ull)))
+                            kq |= 1u << j;
+                    }
+                }
+                unsigned bal = __ballot_sync(kFull, kq != 0u);
+                while (bal) {
+                    const int i = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const int ti = __shfl_sync(kFull, t, i);
+                    unsigned kqi = __shfl_sync(kFull, kq, i);
+                    int dri[G];
+#pragma unroll
+                    for (int j = 0; j < G; ++j) dri[j] = __shfl_sync(kFull, dr[j], i);
+                    uint64_t F[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) F[w] = p.hm[(b + i) * W + w];
+                    const double *qs = p.sigma + (size_t)ti * S;
+                    while (kqi) {
+                        const int j = __ffs(kqi) - 1;
+                        kqi &= kqi - 1;
+                        int drj = 0;
+#pragma unroll
+                        for (int jj = 0; jj < G; ++jj)
+                            if (jj == j) drj = dri[jj];
+                        const int k = L - drj;
+                        const double rs = p.rsigq[(size_t)ti * 64 + cg + j];
+#pragma unroll
+                        for (int ii = 0; ii < PL; ++ii) {
+                            const int s = lane + 32 * ii;
+                            if (mask_bit<W>(F, s) && s_ql[s * G + j] == k) {
+                                atomicAdd(&s_acc[s * G + j], rs / qs[s]);
+                                ++pairs;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // sigma_s(r_c) times the sums: delta_s.(r_c) parts of this block
+        for (int i = threadIdx.x; i < S * G; i += blockDim.x) {
+            const double a = s_acc[i];
+            if (a != 0.0) {
+                const int sl = i / G, j = i % G;
+                atomicAdd(&p.msum[sl * 64 + cg + j], a * p.sigma[(size_t)p.croot[cg + j] * S + sl]);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+    if (lane == 0 && pairs) atomicAdd(&p.ctr->vpairs, (unsigned long long)pairs);
+}
+
 template <int W, int MODE, int MINB>
 __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
     constexpr int S = 64 * W;
@@ -874,18 +1011,32 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
 
         // ---------------- backward ----------------
         if (MODE == kModeScan && (p.flags & kFlagRootOut)) {
-            // the query vertex's own traversal (source slot 0): keep d(r, t) and sigma_rt
+            // the query vertices' own traversal (source slot c = column c):
+            // keep d(r_c, t) and sigma_{r_c t}
             for (int Lr = 0; Lr <= Lmax; ++Lr) {
                 const long long eend = p.lev_start[Lr + 1];
                 for (long long e = p.lev_start[Lr] + gthr; e < eend; e += nthr) {
                     const int v = p.hv[e];
-                    p.rlev[v] = Lr;
-                    p.rsig[v] = p.sigma[(size_t)v * S];
+                    if (p.ncols >= 2) {
+                        uint64_t x = p.hm[(size_t)e * W];  // columns sit in the first mask word
+                        while (x) {
+                            const int c = __ffsll((long long)x) - 1;
+                            x &= x - 1;
+                            p.rlevq[(size_t)v * 64 + c] = Lr;
+                            p.rsigq[(size_t)v * 64 + c] = p.sigma[(size_t)v * S + c];
+                        }
+                    } else {
+                        p.rlev[v] = Lr;
+                        p.rsig[v] = p.sigma[(size_t)v * S];
+                    }
                 }
             }
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
         } else if (MODE == kModeScan && !(p.flags & kFlagNoBackward)) {
-            vertex_scan<W>(p, Lmax, s_need, gwarp, nwarps);
+            if (p.ncols >= 2)
+                vertex_scan_multi<W>(p, Lmax, s_need, gwarp, nwarps);
+            else
+                vertex_scan<W>(p, Lmax, s_need, gwarp, nwarps);
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
         }
         if (MODE == kModeSpd && !(p.flags & kFlagNoBackward)) {
@@ -957,14 +1108,14 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
 
         // ---------------- tile end ----------------
         if (MODE == kModeScan && blockIdx.x == 0) {
-            // every query of a scan launch has the same vertex: one sum per source
+            // one sum per source (one query vertex) or per (source, column)
             for (int s = threadIdx.x; s < S; s += blockDim.x) {
                 uint64_t x = s_need[s];
                 const double d = p.vsum[s];
                 while (x) {
                     const int q = __ffsll((long long)x) - 1;
                     x &= x - 1;
-                    p.dep[s * 64 + q] = d;
+                    p.dep[s * 64 + q] = p.ncols >= 2 ? p.msum[s * 64 + p.qcol[q]] : d;
                 }
             }
             __syncthreads();

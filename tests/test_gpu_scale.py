@@ -147,6 +147,25 @@ def test_rmat20_full_tile_probe(bcd, rmat20):
                     assert close(dep[i, j], st["delta"][t]), (i, s, t, dep[i, j], st["delta"][t])
 
 
+def test_rmat20_multi_vertex_scan(bcd, rmat20):
+    """accumulation = 3 at full size: 8 of the bench's queries (4 uniform,
+    4 of largest in*out degree) in one group, A-BCD with 32 draws each
+    (seed 7), against the oracle's A-BCD on the same draws."""
+    g, og, dg, qs = rmat20
+    pick = [q for q in qs[:32] if g.out_degree()[q] > 0][:4] + qs[32:36]
+    specs = [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 32, "seed": 7} for r in pick]
+    bcd.bc_set_config(dg, accumulation=3)
+    try:
+        out, info = bcd.bc_batch(dg, specs)
+    finally:
+        bcd.bc_set_config(dg, accumulation=1)
+    assert info["scan_pairs"] > 0
+    threads = os.cpu_count() or 1
+    for r, o in zip(pick, out):
+        want = O.bc_approx(og, r, 32, 7, threads)[0]
+        assert o["status"] == 0 and close(o["bc"], want), (r, o["bc"], want)
+
+
 @pytest.fixture(scope="module")
 def rmat22(bcd):
     g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)

@@ -57,13 +57,18 @@ def sparse_er():
 def test_config_roundtrip(bcd, er1):
     g, _ = er1
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
-    assert bcd.bc_get_config(dg)["accumulation"] == 2
+    assert bcd.bc_get_config(dg)["accumulation"] == 4
     bcd.bc_set_config(dg, accumulation=1)
     assert bcd.bc_get_config(dg)["accumulation"] == 1
     bcd.bc_set_config(dg, accumulation=2)
     assert bcd.bc_get_config(dg)["accumulation"] == 2
+    bcd.bc_set_config(dg, accumulation=3)
+    assert bcd.bc_get_config(dg)["accumulation"] == 3
+    bcd.bc_set_config(dg, accumulation=4)
+    assert bcd.bc_get_config(dg)["accumulation"] == 4
+    bcd.bc_set_config(dg, accumulation=2)
     with pytest.raises(bcd.BCError) as e:
-        bcd.bc_set_config(dg, accumulation=3)
+        bcd.bc_set_config(dg, accumulation=5)
     assert e.value.status == bcd.BC_E_INVALID_ARG
     # a tile's sources are seeded one per thread
     bcd.bc_set_config(dg, tile_words=2, block_threads=128)
@@ -326,3 +331,123 @@ def test_scan_repeated_launches(bcd, er1):
             got = bcd.bc_exact(dg, r)[0]
             assert close(got, want[r]), (it, r, got, want[r])
         dg.close()
+
+
+# ------------------------------------------------ several query vertices (accumulation = 3)
+
+@pytest.mark.parametrize("cfg", [{}, {"tile_words": 1}, {"tile_words": 2, "chunk_arcs": 32},
+                                 {"tile_words": 4, "blocks_per_sm": 1}])
+def test_multi_vertex_scan_exact(bcd, er1, cfg):
+    """A batch of exact queries at 20 distinct vertices (three passes of 8
+    columns) with repeated vertices, against the oracle's E-BCD."""
+    g, og = er1
+    dg = make(bcd, g, **cfg)
+    bcd.bc_set_config(dg, accumulation=3)
+    rs = gg.random_vertices(g.n, 20, 61).tolist()
+    rs = rs + rs[:3]
+    out, info = bcd.bc_batch(dg, [{"r": r} for r in rs])
+    assert info["scan_pairs"] > 0
+    for r, o in zip(rs, out):
+        assert o["status"] == 0
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), (cfg, r, o["bc"])
+
+
+def test_multi_vertex_scan_mixed_kinds(bcd, er1):
+    """64 queries at up to 64 distinct vertices in one group: exact, sampled
+    (shared and own seeds), hybrid; several kinds at one vertex."""
+    g, og = er1
+    dg = make(bcd, g)
+    bcd.bc_set_config(dg, accumulation=3)
+    rs = gg.random_vertices(g.n, 56, 62).tolist()
+    specs = []
+    for i, r in enumerate(rs):
+        k = i % 4
+        if k == 0:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_EXACT})
+        elif k == 1:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 600, "seed": 7})
+        elif k == 2:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 300, "seed": 1000 + i})
+        else:
+            specs.append({"r": r, "kind": bcd.BC_QUERY_HYBRID, "T": 1000, "seed": 3})
+    for r in rs[:8]:
+        specs.append({"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 200, "seed": 9})
+    assert len(specs) == 64
+    out, info = bcd.bc_batch(dg, specs)
+    for s, o in zip(specs, out):
+        r = s["r"]
+        rvk = O.rv(og, r).shape[0]
+        if s["kind"] == bcd.BC_QUERY_EXACT or (s["kind"] == bcd.BC_QUERY_HYBRID and rvk <= s["T"]):
+            want = O.bc_exact(og, r, 0)[0]
+        else:
+            want = O.bc_approx(og, r, s["T"], s["seed"], 0)[0]
+        assert o["status"] == 0 and close(o["bc"], want), (s, o["bc"], want)
+
+
+def test_multi_vertex_scan_edge_cases(bcd, sparse_er):
+    """Sparse ER (many small reach sets, long levels): queries with empty
+    RV and out-degree 0 beside ordinary ones; 2^k path counts on a diamond
+    chain with the sink and a middle vertex as two query vertices."""
+    g, og = sparse_er
+    dg = make(bcd, g)
+    bcd.bc_set_config(dg, accumulation=3)
+    rs = gg.random_vertices(g.n, 40, 63).tolist()
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in rs])
+    for r, o in zip(rs, out):
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), r
+    k = 40
+    arcs = []
+    for i in range(k):
+        a, b, c, d = 3 * i, 3 * i + 1, 3 * i + 2, 3 * i + 3
+        arcs += [(a, b), (a, c), (b, d), (c, d)]
+    arcs.append((3 * k, 3 * k + 1))
+    gd = csr(3 * k + 2, arcs)
+    ogd = O.Graph.from_csr(gd)
+    dgd = make(bcd, gd)
+    bcd.bc_set_config(dgd, accumulation=3)
+    qs = [3 * k, 3 * (k // 2), 3 * (k // 2) + 1, 0]
+    out, _ = bcd.bc_batch(dgd, [{"r": r} for r in qs])
+    for r, o in zip(qs, out):
+        assert close(o["bc"], O.bc_exact(ogd, r, 0)[0]), r
+
+
+def test_multi_vertex_scan_weighted_keeps_eq4(bcd):
+    """On a weighted graph accumulation 3 keeps the one-vertex scan for
+    one-vertex groups and Eq. 4 for the others; results match the oracle."""
+    g = gg.erdos_renyi(600, 4000, 21)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 3, 4))
+    og = O.Graph.from_csr(g)
+    dg = make(bcd, g)
+    bcd.bc_set_config(dg, accumulation=3)
+    rs = gg.random_vertices(g.n, 6, 64).tolist()
+    out, info = bcd.bc_batch(dg, [{"r": r} for r in rs])
+    assert info["scan_pairs"] == 0
+    for r, o in zip(rs, out):
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), r
+
+
+def test_auto_choice_per_group(bcd, er1):
+    """accumulation = 4 (the default): on ER (no hubs) a group of 12 vertices
+    keeps the scan after its first tile; with a hub among the query
+    vertices (20,000 in- and out-arcs: nearly every shortest path runs
+    through it) the first tile's terms outnumber the push's and the other
+    tiles take Eq. 4. Results match the oracle either way."""
+    g, og = er1
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    bcd.bc_set_config(dg, tile_words=1)
+    rs = gg.random_vertices(g.n, 12, 65).tolist()
+    out, info = bcd.bc_batch(dg, [{"r": r} for r in rs])
+    assert info["tiles"] > 1 and info["scan_tiles"] == info["tiles"], info
+    for r, o in zip(rs, out):
+        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), r
+    n = 20001
+    arcs = [(0, i) for i in range(1, n)] + [(i, 0) for i in range(1, n)]
+    arcs += [(i, i + 1) for i in range(1, n - 1)]
+    gh = csr(n, arcs)
+    ogh = O.Graph.from_csr(gh)
+    dgh = bcd.bc_graph_create(gh.n, gh.offsets, gh.cols)
+    qs = [0, 17, 5000]
+    out, info = bcd.bc_batch(dgh, [{"r": r} for r in qs])
+    assert info["tiles"] > 1 and info["scan_tiles"] == 1, info
+    for r, o in zip(qs, out):
+        assert close(o["bc"], O.bc_exact(ogh, r, 0)[0]), r
