@@ -266,11 +266,16 @@ def solve_step(bcd, dg, specs, rank, world, dist):
 
 
 def algorithmic_bytes(info):
-    """The kernel's algorithmic bytes for a launch (see the design notes):
-    graph structure 2 (8 |V_B| + 4 |E_B|) summed over tiles, 40 bytes per
-    reached (source, vertex) pair and 24 per tight (source, arc) pair."""
-    return (2.0 * (8.0 * info["union_vertices"] + 4.0 * info["union_arcs"]) + 40.0 * info["reached_pairs"] +
-            24.0 * info["tight_pairs"])
+    """The traversal's algorithmic bytes (see the design notes): graph
+    structure 2 (8 |V_B| + 4 |E_B|) summed over tiles; the forward pass, 24
+    bytes per reached (source, vertex) pair (level and sigma written and read
+    back) and 8 per tight (source, arc) pair (sigma of the tail); the Eq. 4
+    backward, on the tiles that ran it, 16 more per reached pair (delta
+    written and read) and 16 per tight pair (sigma and delta of the head);
+    the vertex scan, 16 per term (sigma_st and sigma_rt)."""
+    return (2.0 * (8.0 * info["union_vertices"] + 4.0 * info["union_arcs"]) + 24.0 * info["reached_pairs"] +
+            8.0 * info["tight_pairs"] + 16.0 * info["eq4_reached_pairs"] + 16.0 * info["eq4_tight_pairs"] +
+            16.0 * info["scan_pairs"])
 
 
 def run_gpu(args):

@@ -210,6 +210,8 @@ typedef struct {
                                  query vertex (inside ms_spd, not in ms_traversal) */
     int64_t pull_levels;      /* forward levels run bottom-up (bc_config.pull_permille) */
     int64_t scan_tiles;       /* tiles whose dependencies came from the vertex scan */
+    int64_t eq4_reached_pairs; /* reached_pairs and tight_pairs of the tiles that ran the */
+    int64_t eq4_tight_pairs;   /* backward pass of Eq. 4 (the others ran the vertex scan) */
 } bc_batch_info;
 
 /*

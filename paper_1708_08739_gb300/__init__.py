@@ -72,7 +72,8 @@ class bc_batch_info(C.Structure):
                 ("grid_blocks", C.c_int32), ("ms_traversal", C.c_double), ("reached_pairs", C.c_int64),
                 ("tight_pairs", C.c_int64), ("arc_visits", C.c_int64), ("union_vertices", C.c_int64),
                 ("union_arcs", C.c_int64), ("scan_pairs", C.c_int64), ("ms_root", C.c_double),
-                ("pull_levels", C.c_int64), ("scan_tiles", C.c_int64)]
+                ("pull_levels", C.c_int64), ("scan_tiles", C.c_int64), ("eq4_reached_pairs", C.c_int64),
+                ("eq4_tight_pairs", C.c_int64)]
 
 
 class bc_config(C.Structure):

@@ -150,8 +150,8 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->source_order && c->source_order != 1 && c->source_order != 2)
         return set_error(BC_E_INVALID_ARG, "bc_set_config: source_order must be 1 or 2");
     if (c->source_order) g->source_order = c->source_order == 1 ? 1 : 0;
-    if (c->blocks_per_sm && c->blocks_per_sm != 1 && c->blocks_per_sm != 2)
-        return set_error(BC_E_INVALID_ARG, "bc_set_config: blocks_per_sm must be 1 or 2");
+    if (c->blocks_per_sm && (c->blocks_per_sm < 1 || c->blocks_per_sm > 3))
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: blocks_per_sm must be 1, 2 or 3");
     if (c->blocks_per_sm) g->blocks_per_sm = c->blocks_per_sm;
     if (c->weighted_words) {
         const int w = c->weighted_words;

@@ -473,6 +473,7 @@ struct GroupTimes {
     int64_t sources = 0;
     int64_t tiles = 0;
     int64_t scan_tiles = 0;  // tiles whose dependencies came from the vertex scan
+    unsigned long long eq4_reached = 0, eq4_tight = 0;  // reached / tight pairs of the Eq. 4 tiles
     unsigned long long edges = 0;
     int levels = 0;
 };
@@ -978,6 +979,10 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
             tm.c.eb += c.eb;
             tm.c.vpairs += c.vpairs;
             tm.c.pull_levels += c.pull_levels;
+            if (!scan_mode) {
+                tm.eq4_reached += c.reached;
+                tm.eq4_tight += c.tight;
+            }
             return BC_OK;
         };
         std::vector<uint32_t> cal_flags(64, 0);
@@ -1262,6 +1267,8 @@ static bc_status run_batch(bc_graph *g, const bc_query *queries, int64_t nq, bc_
         bi.scan_pairs += (int64_t)t.c.vpairs;
         bi.pull_levels += (int64_t)t.c.pull_levels;
         bi.scan_tiles += t.scan_tiles;
+        bi.eq4_reached_pairs += (int64_t)t.eq4_reached;
+        bi.eq4_tight_pairs += (int64_t)t.eq4_tight;
         bi.ms_root += t.root;
         group.clear();
         return BC_OK;

@@ -220,11 +220,10 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
         for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
         double sig[PL];
         if (MODE != kModeReach) {
-#pragma unroll
-            for (int ii = 0; ii < PL; ++ii) sig[ii] = p.sigma[(size_t)v * S + lane + 32 * ii];
+            // only the frontier's sources: sectors of the row without one are not read
 #pragma unroll
             for (int ii = 0; ii < PL; ++ii)
-                if (!mask_bit<W>(F, lane + 32 * ii)) sig[ii] = 0.0;
+                sig[ii] = mask_bit<W>(F, lane + 32 * ii) ? p.sigma[(size_t)v * S + lane + 32 * ii] : 0.0;
         }
         if (ch.k == 0) {
             if (MODE == kModeReach && p.levout && lane == 0 && p.levout[v] < 0) p.levout[v] = L;
@@ -1275,7 +1274,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             if (W == 1)
                 st = launch<1, kModeScan, 2>(g, p);
             else if (W == 2)
-                st = launch<2, kModeScan, 2>(g, p);
+                st = g->blocks_per_sm == 3 ? launch<2, kModeScan, 3>(g, p) : launch<2, kModeScan, 2>(g, p);
             else if (W == 4)
                 st = g->blocks_per_sm == 2 ? launch<4, kModeScan, 2>(g, p) : launch<4, kModeScan, 1>(g, p);
             else
@@ -1283,7 +1282,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
         } else if (W == 1) {
             st = launch<1, kModeSpd, 2>(g, p);
         } else if (W == 2) {
-            st = launch<2, kModeSpd, 2>(g, p);
+            st = g->blocks_per_sm == 3 ? launch<2, kModeSpd, 3>(g, p) : launch<2, kModeSpd, 2>(g, p);
         } else if (W == 4) {
             st = g->blocks_per_sm == 2 ? launch<4, kModeSpd, 2>(g, p) : launch<4, kModeSpd, 1>(g, p);
         } else {
