@@ -383,6 +383,11 @@ void bc_server_destroy(bc_server *srv);
  *                  arc), the others top-down (the frontier pushes sigma
  *                  along its out-arcs); 1..1000, or -1 for top-down only.
  *                  Results are identical either way (sigma sums integers).
+ *   weighted_short_row  weighted kernel: a settled (vertex, source) pair
+ *                  whose in- and out-rows both have at most this many arcs
+ *                  is handled by one lane; longer rows are cut into
+ *                  chunk_arcs chunks that a warp takes with lanes over arcs
+ *                  (1..1024, default 32).
  *   timeout_us     limit, in microseconds of wall time, on every wait of a
  *                  traversal kernel at a grid-wide barrier (default
  *                  10,000,000: 10 s). A wait that runs out makes every block
@@ -400,10 +405,40 @@ typedef struct {
     int32_t accumulation;
     int32_t timeout_us;
     int32_t pull_permille;
+    int32_t weighted_short_row;
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);
 bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
+
+/*
+ * Autotuner of the batched traversal's launch parameters for a graph and a
+ * kind of batch. The probe batch is queries[0 .. min(nq, 64)) with every
+ * query turned into A-BCD with min(T, probe_T) draws (same vertices and
+ * seeds), so each candidate costs a few tiles. Starting from the graph's
+ * current configuration, one parameter at a time takes each of its
+ * candidate values with the others fixed, and the fastest (CUDA-event time
+ * of the batch, second of two runs) is kept:
+ *   unweighted: tile_words 2, 4; blocks_per_sm 1, 2; chunk_arcs 64, 128, 256;
+ *               pull_permille -1, 200; accumulation 1, 4;
+ *   weighted:   weighted_words 2, 4, 8; weighted_short_row 16, 32, 64;
+ *               chunk_arcs 64, 128, 256; accumulation 1, 4.
+ * Candidates that do not fit in device memory are skipped. The winner is
+ * applied to g and written to *best; rep (may be NULL) receives the number
+ * of candidates timed and the probe times of the starting and the chosen
+ * configuration. Results of later calls are unchanged beyond fp64 summation
+ * order. Errors: BC_E_INVALID_ARG (nq < 1, probe_T outside 1..10^6), and
+ * those of bc_batch (the starting configuration is restored).
+ */
+typedef struct {
+    int64_t candidates;     /* configurations timed */
+    int64_t probe_queries;  /* queries in the probe batch */
+    double ms_default;      /* probe time of the starting configuration */
+    double ms_best;         /* probe time of the chosen one */
+} bc_tune_report;
+
+bc_status bc_tune(bc_graph *g, const bc_query *queries, int64_t nq, int64_t probe_T, bc_config *best,
+                  bc_tune_report *rep);
 
 /*
  * RV(r) for callers that cannot allocate device memory. (The paper has no

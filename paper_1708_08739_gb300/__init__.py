@@ -79,7 +79,13 @@ class bc_batch_info(C.Structure):
 class bc_config(C.Structure):
     _fields_ = [("tile_words", C.c_int32), ("chunk_arcs", C.c_int32), ("block_threads", C.c_int32),
                 ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("weighted_words", C.c_int32),
-                ("accumulation", C.c_int32), ("timeout_us", C.c_int32), ("pull_permille", C.c_int32)]
+                ("accumulation", C.c_int32), ("timeout_us", C.c_int32), ("pull_permille", C.c_int32),
+                ("weighted_short_row", C.c_int32)]
+
+
+class bc_tune_report(C.Structure):
+    _fields_ = [("candidates", C.c_int64), ("probe_queries", C.c_int64), ("ms_default", C.c_double),
+                ("ms_best", C.c_double)]
 
 
 class bc_server_config(C.Structure):
@@ -124,6 +130,8 @@ _SIGNATURES = {
     "bc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(bc_result), C.POINTER(C.c_double), C.c_int64]),
     "bc_server_stats_get": (C.c_int, [C.c_void_p, C.POINTER(bc_server_stats)]),
     "bc_server_destroy": (None, [C.c_void_p]),
+    "bc_tune": (C.c_int, [C.c_void_p, C.POINTER(bc_query), C.c_int64, C.c_int64, C.POINTER(bc_config),
+                          C.POINTER(bc_tune_report)]),
     "bc_cancel": (C.c_int, [C.c_void_p]),
     "bc_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "bc_last_error": (C.c_char_p, []),
@@ -230,9 +238,10 @@ def bc_set_stream(g: Graph, stream):
 
 
 def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0,
-                  weighted_words=0, accumulation=0, timeout_us=0, pull_permille=0):
+                  weighted_words=0, accumulation=0, timeout_us=0, pull_permille=0, weighted_short_row=0):
     c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm),
-                  int(weighted_words), int(accumulation), int(timeout_us), int(pull_permille))
+                  int(weighted_words), int(accumulation), int(timeout_us), int(pull_permille),
+                  int(weighted_short_row))
     _check(lib().bc_set_config(g.handle, C.byref(c)))
 
 
@@ -240,6 +249,17 @@ def bc_get_config(g: Graph) -> dict:
     c = bc_config()
     _check(lib().bc_get_config(g.handle, C.byref(c)))
     return {k: getattr(c, k) for k, _ in bc_config._fields_}
+
+
+def bc_tune(g: Graph, specs, probe_T=256):
+    """Times candidate launch parameters on a probe of the batch `specs`
+    (every query as A-BCD with at most probe_T draws), applies the fastest to
+    g and returns (config dict, report dict)."""
+    q, nq = make_queries(specs)
+    c = bc_config()
+    rep = bc_tune_report()
+    _check(lib().bc_tune(g.handle, q, nq, int(probe_T), C.byref(c), C.byref(rep)))
+    return {k: getattr(c, k) for k, _ in bc_config._fields_}, {k: getattr(rep, k) for k, _ in bc_tune_report._fields_}
 
 
 def bc_cancel(g: Graph):

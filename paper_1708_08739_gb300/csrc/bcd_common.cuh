@@ -135,6 +135,7 @@ struct TravParams {
     int64_t bcap;            // entries per slot (a power of two)
     int32_t ring;            // power of two above the largest weight
     int32_t nw;              // 64-source words of a weighted tile (1, 2, 4, 8 or 16)
+    int32_t wshort;          // weighted: rows of at most this many arcs are walked by one lane
     int64_t *lev_dist;       // [maxlev + 2] distance of each non-empty level
     // vertex scan (one query vertex vroot): its forward traversal and per-source sums
     int32_t *rlev;           // [n] d(vroot, t), -1 unreached (unweighted)
@@ -283,6 +284,7 @@ struct bc_graph {
     int block_threads = 512;
     int accumulation = 4;         // 1: Eq. 4 push, 2: vertex scan for one-vertex groups, 3: scan always, 4: chosen per group
     int pull_permille = 0;        // bottom-up levels: frontier out-arcs >= pull_permille / 1000 of m (0: never)
+    int wshort = 32;              // weighted kernel: longest row one lane walks alone
     bcd_workspace ws;
     int64_t launches = 0;
     int last_grid = 0;                       // blocks of the last traversal launch

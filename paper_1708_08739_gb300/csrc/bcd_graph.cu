@@ -172,6 +172,9 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->pull_permille && (c->pull_permille < -1 || c->pull_permille > 1000))
         return set_error(BC_E_INVALID_ARG, "bc_set_config: pull_permille must be 1..1000 or -1 (0 keeps it)");
     if (c->pull_permille) g->pull_permille = c->pull_permille < 0 ? 0 : c->pull_permille;
+    if (c->weighted_short_row && (c->weighted_short_row < 1 || c->weighted_short_row > 1024))
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: weighted_short_row must be 1..1024 (0 keeps it)");
+    if (c->weighted_short_row) g->wshort = c->weighted_short_row;
     if (c->timeout_us) g->timeout_ns = 1000.0 * (double)c->timeout_us;
     if (c->accumulation) g->accumulation = c->accumulation;
     if (c->tile_words) g->tile_words = c->tile_words;
@@ -191,6 +194,7 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->accumulation = g->accumulation;
     c->timeout_us = (int32_t)(g->timeout_ns / 1000.0);
     c->pull_permille = g->pull_permille > 0 ? g->pull_permille : -1;
+    c->weighted_short_row = g->wshort;
     return BC_OK;
 }
 

@@ -1465,6 +1465,89 @@ bc_status bc_draw_samples(bc_graph *g, int32_t r, int64_t T, uint64_t seed, int3
     return BC_OK;
 }
 
+// Autotuner: coordinate descent over the launch parameters, each candidate
+// timed (CUDA events of the group, second of two runs) on a probe batch made
+// of the caller's queries with every query turned into A-BCD with at most
+// probe_T draws (same vertices and seeds, so the same mix of query vertices
+// and the same shape of source sets, at a small cost per candidate).
+bc_status bc_tune(bc_graph *g, const bc_query *queries, int64_t nq, int64_t probe_T, bc_config *best,
+                  bc_tune_report *rep) {
+    if (!g || !best || (nq > 0 && !queries) || nq < 1) return set_error(BC_E_INVALID_ARG, "bc_tune: bad arguments");
+    if (probe_T < 1 || probe_T > 1000000) return set_error(BC_E_INVALID_ARG, "bc_tune: probe_T must be 1..10^6");
+    const int64_t n = std::min<int64_t>(nq, 64);
+    std::vector<bc_query> probe((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        probe[i] = queries[i];
+        int64_t T = probe_T;
+        if (queries[i].kind == BC_QUERY_APPROX_T) T = std::min<int64_t>(queries[i].T, probe_T);
+        probe[i].kind = BC_QUERY_APPROX_T;
+        probe[i].T = T;
+    }
+    std::vector<bc_result> out((size_t)n);
+    bc_config cur;
+    BCD_TRY(bc_get_config(g, &cur));
+    const bc_config start = cur;
+    int runs = 0;
+    auto timed = [&](const bc_config &c, double *ms) -> bc_status {
+        BCD_TRY(bc_set_config(g, &c));
+        bc_batch_info bi;
+        BCD_TRY(run_batch(g, probe.data(), n, out.data(), &bi));  // warm (workspace, chunk lists)
+        BCD_TRY(run_batch(g, probe.data(), n, out.data(), &bi));
+        *ms = bi.ms_total;
+        ++runs;
+        return BC_OK;
+    };
+    double best_ms = 0.0;
+    BCD_TRY(timed(cur, &best_ms));
+    const double start_ms = best_ms;
+    // the search space, one parameter at a time (0 ends a list)
+    std::vector<std::pair<int32_t bc_config::*, std::vector<int32_t>>> space;
+    if (g->weighted) {
+        space.push_back({&bc_config::weighted_words, {2, 4, 8}});
+        space.push_back({&bc_config::weighted_short_row, {16, 32, 64}});
+        space.push_back({&bc_config::chunk_arcs, {64, 128, 256}});
+        space.push_back({&bc_config::accumulation, {1, 4}});
+    } else {
+        space.push_back({&bc_config::tile_words, {2, 4}});
+        space.push_back({&bc_config::blocks_per_sm, {1, 2}});
+        space.push_back({&bc_config::chunk_arcs, {64, 128, 256}});
+        space.push_back({&bc_config::pull_permille, {-1, 200}});
+        space.push_back({&bc_config::accumulation, {1, 4}});
+    }
+    for (auto &dim : space) {
+        for (int32_t val : dim.second) {
+            if (cur.*(dim.first) == val) continue;
+            bc_config c = cur;
+            c.*(dim.first) = val;
+            if (!g->weighted && c.block_threads < 64 * c.tile_words) continue;
+            if ((((uint64_t)g->n) << 6) * (uint64_t)c.weighted_words > (1ull << 32)) continue;
+            double ms = 0.0;
+            bc_status st = timed(c, &ms);
+            if (st == BC_E_OOM) {  // a wider tile that does not fit: skip it
+                BCD_TRY(bc_set_config(g, &cur));
+                continue;
+            }
+            if (st != BC_OK) {
+                bc_set_config(g, &start);
+                return st;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                cur = c;
+            }
+        }
+    }
+    BCD_TRY(bc_set_config(g, &cur));
+    *best = cur;
+    if (rep) {
+        rep->candidates = runs;
+        rep->ms_default = start_ms;
+        rep->ms_best = best_ms;
+        rep->probe_queries = n;
+    }
+    return BC_OK;
+}
+
 bc_status bc_spd_probe(bc_graph *g, const int32_t *sources, int32_t nsrc, const int32_t *targets, int32_t nt,
                        uint64_t *dist, double *sigma, double *dep, uint32_t *flags) {
     if (!g || (nsrc > 0 && !sources) || (nt > 0 && !targets))

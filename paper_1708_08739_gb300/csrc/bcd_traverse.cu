@@ -1268,6 +1268,7 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
             p.bcap = ws.bcap;
             p.ring = ws.ring;
             p.nw = W;
+            p.wshort = g->wshort;
             p.lev_dist = ws.lev_dist;
             st = launch_weighted(g, p);
         } else if (p.mode == kModeScan) {

@@ -46,7 +46,6 @@ namespace {
 using namespace dev;
 
 constexpr int kMaxWords = 16;  // largest tile: 1024 sources
-constexpr int kShortRow = 32;  // rows of at most this many arcs are walked by one lane
 constexpr double kTwo53 = 9007199254740992.0;
 
 // Per-level counters of the weighted kernel: counter k of level l sits at
@@ -362,7 +361,7 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                         }
                     }
                     double *sp = p.sigma + ((size_t)x << tl.shift) + s;
-                    if (re - rb <= kShortRow && ire - irb <= kShortRow) {
+                    if (re - rb <= p.wshort && ire - irb <= p.wshort) {
                         const double sg = d > 0 ? pull_sigma(p, tl, s, du, irb, ire, 1, st.tight) : 1.0;
                         *sp = sg;
                         if (sg >= kTwo53) flag_source(p, s);
@@ -511,7 +510,7 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                         if (s_minql[s] > sg) continue;
                         const int v = p.hv[e];
                         const long long rb = __ldg(p.off + v), re = __ldg(p.off + v + 1);
-                        if (re - rb <= kShortRow) {
+                        if (re - rb <= p.wshort) {
                             const double acc = pull_c(p, tl, s, dk, rb, re, 1);
                             wfinalize(p, tl, s_need, v, s, acc);
                             st.arcs += (unsigned)(re - rb);

@@ -60,7 +60,7 @@ def test_no_oracle_in_product_path():
 
 
 STRUCTS = ["bc_graph_desc", "bc_info", "bc_query", "bc_result", "bc_batch_info", "bc_config", "bc_server_config",
-           "bc_server_stats"]
+           "bc_server_stats", "bc_tune_report"]
 
 
 def test_binding_struct_layouts_match_the_header(built_lib, tmp_path):
