@@ -468,6 +468,18 @@ def serve_workload(bcd, dg, g, nq, rv_max, seed=106):
     until 1 <= |RV(r)| <= rv_max; sampled ones until |RV(r)| >= 1 (on this
     graph |RV| is either tiny or the whole giant in-component, which only
     sampling serves)."""
+    # host-side screen of the synthetic workload: a vertex with no in-arc has
+    # |RV| = 0, and one reachable from the hub (the vertex of largest in x out
+    # degree) has every vertex that reaches the hub in its RV; only the others
+    # need an RV traversal to learn their size
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import breadth_first_order
+    hub = int(gg.top_inout_vertices(g, 1)[0])
+    adj = sp.csr_matrix((np.ones(g.m, dtype=np.int8), g.cols, g.offsets), shape=(g.n, g.n))
+    behind_hub = np.zeros(g.n, dtype=bool)
+    behind_hub[breadth_first_order(adj, hub, directed=True, return_predecessors=False)] = True
+    hub_rv = bcd.bc_rv_compute(dg, hub).shape[0]
+    indeg = np.bincount(g.cols, minlength=g.n)
     sizes = {}
     out = []
     draws = 0
@@ -478,12 +490,20 @@ def serve_workload(bcd, dg, g, nq, rv_max, seed=106):
         for r in cand.tolist():
             draws += 1
             if r not in sizes:
-                sizes[r] = 0 if g.offsets[r + 1] == g.offsets[r] else bcd.bc_rv_compute(dg, r).shape[0]
+                if g.offsets[r + 1] == g.offsets[r] or indeg[r] == 0:
+                    sizes[r] = 0  # out-degree 0 (BC = 0, Prop. 1) or RV empty
+                elif behind_hub[r] and r != hub and hub_rv + 1 > rv_max:
+                    sizes[r] = -1  # |RV| > rv_max: the hub and all that reach it are in RV
+                else:
+                    sizes[r] = bcd.bc_rv_compute(dg, r).shape[0]
             exact = len(out) % 2 == 0
-            if (exact and 1 <= sizes[r] <= rv_max) or (not exact and sizes[r] >= 1):
+            if (exact and 1 <= sizes[r] <= rv_max) or (not exact and (sizes[r] >= 1 or sizes[r] == -1)):
                 out.append(r)
                 if len(out) == nq:
                     break
+    for r in set(out):
+        if sizes[r] == -1:
+            sizes[r] = bcd.bc_rv_compute(dg, r).shape[0]
     specs = []
     for i, r in enumerate(out):
         if i % 2 == 0:
@@ -524,7 +544,12 @@ def serve_run(bcd, srv, specs, rate=None, seed=11):
 
 
 def run_serve(args):
-    """Serving: continuous batching under Poisson arrivals, p50/p99."""
+    """Serving: continuous batching under Poisson arrivals, p50/p99 (the
+    serving shape: R-MAT 22 + 30 % reciprocal resident, Zipf(1.1) query
+    vertices alternating exact and sampled; a closed loop first, then one
+    wave of Poisson arrivals per rate, each a fraction of the closed-loop
+    rate; one query at a time through bc_batch on the first
+    args.serve_single queries)."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
@@ -538,33 +563,45 @@ def run_serve(args):
     specs, draws, rvs = serve_workload(bcd, dg, g, args.serve_queries, args.serve_rv_max)
     log("serve queries: %d (from %d draws), |RV| %d..%d" % (len(specs), draws, min(rvs), max(rvs)))
     srv = bcd.Server(dg)
-    serve_run(bcd, srv, specs[: max(4, len(specs) // 8)])  # warm-up
+    serve_run(bcd, srv, specs[: max(4, min(512, len(specs) // 8))])  # warm-up
+    clk = ClockSampler(0)
+    clk.start()
     wall, lat = serve_run(bcd, srv, specs)
     sat = len(specs) / wall
+    log("closed loop: %.1f queries/s" % sat)
     runs = {"closed_loop": {"queries_per_s": sat, "p50_ms": float(np.percentile(lat, 50)),
-                            "p99_ms": float(np.percentile(lat, 99))}}
-    for f in (0.5, 0.8, 1.0):
+                            "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall}}
+    for f in [float(x) for x in args.serve_rates.split(",") if x]:
         w, l = serve_run(bcd, srv, specs, rate=f * sat, seed=int(100 * f))
         runs["poisson_%.1fx" % f] = {"arrival_rate": f * sat, "queries_per_s": len(specs) / w,
-                                      "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99))}
+                                      "p50_ms": float(np.percentile(l, 50)), "p99_ms": float(np.percentile(l, 99)),
+                                      "wall_s": w}
+        log("poisson %.1fx: p50 %.0f ms p99 %.0f ms" % (f, runs["poisson_%.1fx" % f]["p50_ms"],
+                                                      runs["poisson_%.1fx" % f]["p99_ms"]))
+    clocks = clk.stop()
     st = srv.stats()
     srv.close()
-    # one query at a time, same queries
+    # one query at a time, the first queries of the same list
+    sub = specs[: args.serve_single]
+    lat1 = []
     t = time.time()
-    for s in specs:
-        if s["kind"] == bcd.BC_QUERY_EXACT:
-            bcd.bc_exact(dg, s["r"])
-        else:
-            bcd.bc_approx(dg, s["r"], s["eps"], s["delta"], s["seed"])
-    single = len(specs) / (time.time() - t)
+    for s1 in sub:
+        t1 = time.perf_counter()
+        bcd.bc_batch(dg, [s1])
+        lat1.append(1000.0 * (time.perf_counter() - t1))
+    single = len(sub) / (time.time() - t)
     line = {"metric": METRIC, "value": sat, "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1000.0 * wall, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "serve_rmat22_recip30_zipf", "n": g.n, "m": g.m, "queries": len(specs),
+                       "zipf_draws": draws,
                        "rv_exact_range": [min(rvs[0::2]), max(rvs[0::2])],
                        "rv_sampled_range": [min(rvs[1::2]), max(rvs[1::2])] if len(rvs) > 1 else None,
                        "mix": "alternate exact (|RV| <= %d) / sampled eps 0.02 delta 0.1 seed 7" % args.serve_rv_max},
-            "serving": runs, "one_at_a_time_queries_per_s": single, "server_stats": st}
+            "serving": runs,
+            "one_at_a_time": {"queries": len(sub), "queries_per_s": single, "p50_ms": float(np.percentile(lat1, 50)),
+                              "p99_ms": float(np.percentile(lat1, 99))},
+            "server_stats": st, "clocks": clocks}
     print(json.dumps(line), flush=True)
     dg.close()
 
@@ -737,7 +774,9 @@ def main():
     ap.add_argument("--single-reps", type=int, default=5)
     ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2],
                     help="profile / wprofile cases: 1 Eq. 4 backward (their default), 2 vertex scan")
-    ap.add_argument("--serve-queries", type=int, default=256)
+    ap.add_argument("--serve-queries", type=int, default=10000)
+    ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="Poisson arrival rates as fractions of saturation")
+    ap.add_argument("--serve-single", type=int, default=256, help="queries run one at a time for the comparison")
     ap.add_argument("--serve-rv-max", type=int, default=100000)
     args = ap.parse_args()
     if args.warmup < 3:

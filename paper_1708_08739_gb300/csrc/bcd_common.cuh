@@ -294,6 +294,8 @@ struct bc_graph {
     bcd::Counters last;                           // counters of the last traversal launch
     float last_ms_launch = 0;                // CUDA-event time of the last traversal launch
     double timeout_ns = 10.0e9;              // limit on each grid-barrier wait
+    std::vector<int32_t> root_cache;         // query vertices whose traversal rlev/rsig or rlevq/rsigq hold
+    const void *root_cache_buf = nullptr;    // ... in this buffer (a rebuilt workspace invalidates it)
     int32_t *cancel_h = nullptr;             // pinned, mapped host flag set by bc_cancel
     int32_t *cancel_d = nullptr;             // ... its device address
 };
@@ -344,8 +346,8 @@ struct PrepItem {
 bc_status prepare_sources(bc_graph *g, std::vector<PrepItem> &items);
 bc_status set_query_bit(bc_graph *g, int32_t v, int bit, bool on);
 bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::vector<uint64_t> &needs,
-                    const std::vector<uint32_t> &mult, uint64_t exact_q, std::vector<double> &partials,
-                    uint32_t *qflags, unsigned long long *edges);
+                    const std::vector<uint32_t> &mult, uint64_t exact_q, const std::vector<int32_t> &slot_roots,
+                    std::vector<double> &partials, uint32_t *qflags, unsigned long long *edges);
 bc_status check_graph(bc_graph *g, const char *fn);
 void begin_call(bc_graph *g);
 bc_status prepare_ordering(bc_graph *g);

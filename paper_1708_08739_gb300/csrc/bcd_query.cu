@@ -323,6 +323,8 @@ bc_status ensure_pull_chunks(bc_graph *g) {
 
 void free_workspace(bc_graph *g) {
     bcd_workspace &ws = g->ws;
+    g->root_cache.clear();  // the traversal tables go with the workspace
+    g->root_cache_buf = nullptr;
     dev_free(ws.vs);
     dev_free(ws.tag);
     dev_free(ws.sigma);
@@ -779,6 +781,36 @@ static void shard_tiles(int64_t ntiles, int32_t k, int32_t nshards, int64_t *lo,
 // Runs one group of at most 64 queries whose out-degree is positive; with
 // nshards > 1 only the group's tiles of shard k run, and each score is that
 // shard's part of the sum (already scaled by |RV| / T for sampled queries).
+// The traversal from the query vertices that the vertex scan reads: from one
+// vertex (rlev, rsig) or from several columns (rlevq, rsigq, with the column
+// tables qcol / croot staged in the small buffer). Kept across calls while the
+// ordered list of vertices is unchanged (it depends on the graph only).
+static bc_status scan_roots(bc_graph *g, const std::vector<int32_t> &roots, const std::vector<int32_t> &qcol,
+                            double *ms_root) {
+    bcd_workspace &ws = g->ws;
+    cudaStream_t s = g->stream;
+    if (roots.size() >= 2) {
+        std::vector<int32_t> croot(64, 0);
+        for (size_t c = 0; c < roots.size(); ++c) croot[c] = roots[c];
+        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallQcol, qcol.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallCroot, croot.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        if (g->root_cache == roots && ws.rlevq && g->root_cache_buf == (const void *)ws.rlevq) return BC_OK;
+        g->root_cache.clear();
+        BCD_TRY(root_traversal_multi(g, roots));
+        g->root_cache = roots;
+        g->root_cache_buf = ws.rlevq;
+    } else {
+        const void *buf = g->weighted ? (const void *)ws.rdist : (const void *)ws.rlev;
+        if (g->root_cache == roots && g->root_cache_buf == buf) return BC_OK;
+        g->root_cache.clear();
+        BCD_TRY(root_traversal(g, roots[0]));
+        g->root_cache = roots;
+        g->root_cache_buf = buf;
+    }
+    *ms_root += g->last_ms_launch;
+    return BC_OK;
+}
+
 static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res, GroupTimes &tm, int32_t shard,
                            int32_t nshards) {
     bcd_workspace &ws = g->ws;
@@ -915,17 +947,10 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
     unsigned long long edges = 0;
     const bool scan = nrun > 0 && use_vertex_scan(g, roots.size());
     const bool multi = scan && roots.size() >= 2;
-    if (multi) {
-        std::vector<int32_t> qcol(64, 0), croot(64, 0);
+    if (scan) {
+        std::vector<int32_t> qcol(64, 0);
         for (int i = 0; i < nq; ++i) qcol[i] = qs[i].slot;
-        for (size_t c = 0; c < roots.size(); ++c) croot[c] = roots[c];
-        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallQcol, qcol.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallCroot, croot.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        BCD_TRY(root_traversal_multi(g, roots));
-        tm.root = g->last_ms_launch;
-    } else if (scan) {
-        BCD_TRY(root_traversal(g, roots[0]));
-        tm.root = g->last_ms_launch;
+        BCD_TRY(scan_roots(g, roots, qcol, &tm.root));
     }
     if (nrun > 0) {
         BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, nrun * 64));
@@ -1149,19 +1174,22 @@ __global__ void scatter_need(const int32_t *v, const uint64_t *mask, int64_t cnt
 }
 
 bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::vector<uint64_t> &needs,
-                    const std::vector<uint32_t> &mult, uint64_t exact_q, std::vector<double> &partials,
-                    uint32_t *qflags, unsigned long long *edges) {
+                    const std::vector<uint32_t> &mult, uint64_t exact_q, const std::vector<int32_t> &slot_roots,
+                    std::vector<double> &partials, uint32_t *qflags, unsigned long long *edges) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
-    const int S = 64 * tile_words_of(g);
+    const int W = tile_words_of(g);
+    const int S = 64 * W;
     const int64_t ntiles = (int64_t)srcs.size() / S;
     if (ntiles * S != (int64_t)srcs.size() || ntiles == 0) return set_error(BC_E_INTERNAL, "run_slice: ragged slice");
     std::vector<int32_t> vs;
     std::vector<uint64_t> ms;
+    uint64_t used = 0;  // query slots some source of the slice serves
     for (size_t i = 0; i < srcs.size(); ++i)
         if (srcs[i] >= 0) {
             vs.push_back(srcs[i]);
             ms.push_back(needs[i]);
+            used |= needs[i];
         }
     BCD_CUDA(cudaMemcpyAsync(ws.dlist, srcs.data(), sizeof(int32_t) * srcs.size(), cudaMemcpyHostToDevice, s));
     BCD_TRY(ensure_buf(&ws.draws, &ws.draws_cap, (int64_t)vs.size() * 3 + 4));
@@ -1177,28 +1205,71 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
     }
     BCD_TRY(ensure_buf(&ws.tile_partial, &ws.tile_partial_cap, ntiles * 64));
     BCD_CUDA(cudaMemsetAsync(ws.qflags, 0, 64 * sizeof(uint32_t), s));
-    TravParams p;
-    memset(&p, 0, sizeof(p));
-    p.mode = kModeSpd;
-    p.off = g->d_off;
-    p.col = g->d_col;
-    p.srcs = ws.dlist;
-    p.ntiles = ntiles;
-    p.qmask = ws.qmask;
-    p.need = ws.need;
-    p.exact_q = exact_q;
-    p.mult = any_mult ? ws.mult : nullptr;
-    p.qlevel = ws.qlevel;
-    p.dep = ws.dep;
-    p.tile_partial = ws.tile_partial;
-    p.qflags = ws.qflags;
-    p.srcflag = ws.srcflag;
-    g->launches += 1;
-    BCD_TRY(run_traversal(g, tile_words_of(g), p, nullptr, edges));
+    // the query vertices of the slots this slice serves, as scan columns
+    std::vector<int32_t> roots, qcol(64, 0);
+    for (int q = 0; q < 64; ++q) {
+        if (!((used >> q) & 1ull) || q >= (int)slot_roots.size() || slot_roots[q] < 0) continue;
+        auto it = std::find(roots.begin(), roots.end(), slot_roots[q]);
+        qcol[q] = (int)(it - roots.begin());
+        if (it == roots.end()) roots.push_back(slot_roots[q]);
+    }
+    const bool scan = !roots.empty() && use_vertex_scan(g, roots.size());
+    const bool multi = scan && roots.size() >= 2;
+    double ms_root = 0.0;
+    if (scan) BCD_TRY(scan_roots(g, roots, qcol, &ms_root));
+    auto launch = [&](bool scan_mode, int64_t first, int64_t count) -> bc_status {
+        TravParams p;
+        memset(&p, 0, sizeof(p));
+        p.mode = scan_mode ? kModeScan : kModeSpd;
+        if (scan_mode) {
+            p.rlev = ws.rlev;
+            p.rdist = ws.rdist;
+            p.rsig = ws.rsig;
+            p.vsum = ws.vsum;
+            p.vroot = roots[0];
+        }
+        if (scan_mode && multi) {
+            p.ncols = (int32_t)roots.size();
+            p.qcol = (const int32_t *)(ws.small + kSmallQcol);
+            p.croot = (const int32_t *)(ws.small + kSmallCroot);
+            p.rlevq = ws.rlevq;
+            p.rsigq = ws.rsigq;
+            p.msum = ws.msum;
+        }
+        p.off = g->d_off;
+        p.col = g->d_col;
+        p.srcs = ws.dlist + first * S;
+        p.ntiles = count;
+        p.qmask = ws.qmask;
+        p.need = ws.need;
+        p.exact_q = exact_q;
+        p.mult = any_mult ? ws.mult + (size_t)first * S * 64 : nullptr;
+        p.qlevel = ws.qlevel;
+        p.dep = ws.dep;
+        p.tile_partial = ws.tile_partial + first * 64;
+        p.qflags = ws.qflags;
+        p.srcflag = ws.srcflag;
+        g->launches += 1;
+        unsigned long long ed = 0;
+        BCD_TRY(run_traversal(g, W, p, nullptr, &ed));
+        if (edges) *edges += ed;
+        return BC_OK;
+    };
+    if (edges) *edges = 0;
+    std::vector<uint32_t> cal_flags(64, 0);
+    if (multi && g->accumulation == 4 && ntiles > 1) {
+        BCD_TRY(launch(true, 0, 1));
+        BCD_CUDA(cudaMemcpyAsync(cal_flags.data(), ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        BCD_CUDA(cudaStreamSynchronize(s));
+        BCD_TRY(launch(g->last.vpairs * kScanPairCost <= g->last.tight, 1, ntiles - 1));
+    } else {
+        BCD_TRY(launch(scan, 0, ntiles));
+    }
     partials.resize((size_t)ntiles * 64);
     BCD_CUDA(cudaMemcpyAsync(partials.data(), ws.tile_partial, sizeof(double) * partials.size(), cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaMemcpyAsync(qflags, ws.qflags, 64 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     BCD_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < 64; ++i) qflags[i] |= cal_flags[i];
     return BC_OK;
 }
 

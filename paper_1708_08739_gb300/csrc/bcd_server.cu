@@ -287,7 +287,10 @@ bool bc_server::run_slice_once() {
     uint32_t qflags[64] = {0};
     unsigned long long edges = 0;
     const auto t0 = Clock::now();
-    bc_status st = bcd::run_slice(g, srcs, needs, mult, exact_q, partials, qflags, &edges);
+    std::vector<int32_t> slot_roots(64, -1);
+    for (int sl = 0; sl < 64; ++sl)
+        if (slots[sl]) slot_roots[sl] = slots[sl]->q.r;
+    bc_status st = bcd::run_slice(g, srcs, needs, mult, exact_q, slot_roots, partials, qflags, &edges);
     {
         std::lock_guard<std::mutex> lk(mu);
         stats.busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
