@@ -195,7 +195,7 @@ struct bcd_workspace {
     unsigned long long *lev_cnt = nullptr;
     unsigned long long *lev_ccnt = nullptr;
     unsigned long long *lev_grab = nullptr;  // [6 * (maxlev + 2)]: forward and backward hand-out, in-arc chunk
-                                             // counts, frontier out-arc sums
+                                             // counts, frontier out-arc sums, entries | chunks << 32
     int64_t *lev_start = nullptr;
     int64_t *lev_cstart = nullptr;
     int64_t *lev_icstart = nullptr;

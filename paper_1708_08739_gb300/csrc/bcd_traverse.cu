@@ -75,11 +75,16 @@ __device__ __forceinline__ void warp_append(const TravParams &p, int L, bool app
     for (int o = 16; o > 0; o >>= 1) fa += __shfl_xor_sync(kFull, fa, o);
     unsigned long long eb = 0, cb = 0, ib = 0;
     if (lane == 0) {
-        eb = atomicAdd(&p.lev_cnt[L + 1], (unsigned long long)ne);
-        cb = atomicAdd(&p.lev_ccnt[L + 1], (unsigned long long)tot);
+        // entries (low half) and out-arc chunks (high half) in one atomic: every
+        // appending warp of the level meets on this word
+        const unsigned long long old =
+            atomicAdd(&p.lev_grab[4 * ((long long)p.maxlev + 2) + L + 1], (unsigned long long)ne | ((unsigned long long)tot << 32));
+        eb = old & 0xffffffffull;
+        cb = old >> 32;
         if (MODE == kModeSpd && toti)
             ib = atomicAdd(&p.lev_grab[2 * ((long long)p.maxlev + 2) + L + 1], (unsigned long long)toti);
-        if (MODE != kModeReach && fa) atomicAdd(&p.lev_grab[3 * ((long long)p.maxlev + 2) + L + 1], fa);
+        if (MODE != kModeReach && fa && p.pull_arcs_min > 0)
+            atomicAdd(&p.lev_grab[3 * ((long long)p.maxlev + 2) + L + 1], fa);
     }
     eb = __shfl_sync(kFull, eb, 0);
     cb = __shfl_sync(kFull, cb, 0);
@@ -168,6 +173,7 @@ __device__ void init_tile(const TravParams &p, const int32_t *tsrc) {
     if (t == 0) {
         p.lev_cnt[0] = (unsigned long long)s_valid;
         p.lev_ccnt[0] = (unsigned long long)s_scan[S - 1];
+        p.lev_grab[4 * ((long long)p.maxlev + 2)] = (unsigned long long)s_valid | ((unsigned long long)s_scan[S - 1] << 32);
     }
 }
 
@@ -195,10 +201,13 @@ __device__ __forceinline__ void flush_stats(Counters *c, Stats &st, int lane) {
     st = Stats();
 }
 
+// Expansion of one out-arc chunk of a level-L entry (forward pass): the
+// descriptor, the frontier mask F of its vertex and this lane's first head
+// come in loaded, so the caller can fetch them ahead of time.
 template <int W, int MODE>
-__device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
-                              long long cs1, long long ics1, Stats &st, const uint64_t *s_need,
-                              long long gwarp, long long nwarps) {
+__device__ __forceinline__ void expand_chunk(const TravParams &p, int L, const Chunk &ch, const uint64_t (&F)[W],
+                                             int wv_next, long long es1, long long cs1, long long ics1, Stats &st,
+                                             const uint64_t *s_need) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
     const int lane = threadIdx.x & 31;
@@ -206,145 +215,205 @@ __device__ void forward_level(const TravParams &p, int L, long long cs, long lon
     const int nxt = 1 + ((L + 1) & 1);
     const int stride = p.vs_stride;
     const int CH = p.chunk_arcs;
-    ChunkGrabber grab(&p.lev_grab[L], ccnt, nwarps);
-    long long c;
-    while (grab.next(c, lane)) {
-        const Chunk ch = load_chunk(&p.chunks[cs + c]);
-        const int v = ch.v, e = ch.e;
-        const long long a0 = ch.a0;
-        const int na = ch.na;
-        int wv_next = lane < na ? p.col[a0 + lane] : 0;
-        const uint64_t *vrow = p.vs + (size_t)v * stride;
-        uint64_t F[W];
+    const int v = ch.v, e = ch.e;
+    const long long a0 = ch.a0;
+    const int na = ch.na;
+    double sig[PL];
+    if (MODE != kModeReach) {
+        // only the frontier's sources: sectors of the row without one are not read
 #pragma unroll
-        for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
-        double sig[PL];
+        for (int ii = 0; ii < PL; ++ii)
+            sig[ii] = mask_bit<W>(F, lane + 32 * ii) ? p.sigma[(size_t)v * S + lane + 32 * ii] : 0.0;
+    }
+    if (ch.k == 0) {
+        if (MODE == kModeReach && p.levout && lane == 0 && p.levout[v] < 0) p.levout[v] = L;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w) p.hm[(size_t)e * W + w] = F[w];
+        // visited |= F: reductions that need no answer (the sources of F are
+        // already excluded from new bits by the current-level mask)
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            if (lane == w) atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + w], (unsigned long long)F[w]);
         if (MODE != kModeReach) {
-            // only the frontier's sources: sectors of the row without one are not read
+            if (lane == 0) {
+                int pc = 0;
 #pragma unroll
-            for (int ii = 0; ii < PL; ++ii)
-                sig[ii] = mask_bit<W>(F, lane + 32 * ii) ? p.sigma[(size_t)v * S + lane + 32 * ii] : 0.0;
-        }
-        if (ch.k == 0) {
-            if (MODE == kModeReach && p.levout && lane == 0 && p.levout[v] < 0) p.levout[v] = L;
+                for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
+                st.edges += (unsigned)pc * (unsigned)ch.pad;  // out-degree of v rides in the chunk
+                st.reached += (unsigned)pc;
+            }
+            const uint64_t qm = p.qmask[v];
 #pragma unroll
-            for (int w = 0; w < W; ++w)
-                if (lane == w) p.hm[(size_t)e * W + w] = F[w];
-            // visited |= F: reductions that need no answer (the sources of F are
-            // already excluded from new bits by the current-level mask)
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-                if (lane == w) atomicOr((unsigned long long *)&p.vs[(size_t)v * stride + w], (unsigned long long)F[w]);
-            if (MODE != kModeReach) {
-                if (lane == 0) {
-                    int pc = 0;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) pc += __popcll(F[w]);
-                    st.edges += (unsigned)pc * (unsigned)ch.pad;  // out-degree of v rides in the chunk
-                    st.reached += (unsigned)pc;
+            for (int ii = 0; ii < PL; ++ii) {
+                const int s = lane + 32 * ii;
+                if (mask_bit<W>(F, s)) {
+                    if (qm) {
+                        uint64_t x = qm & s_need[s];
+                        while (x) {
+                            const int q = __ffsll((long long)x) - 1;
+                            x &= x - 1;
+                            p.qlevel[s * 64 + q] = L;
+                        }
+                    }
+                    if (sig[ii] >= 9007199254740992.0)
+                        atomicOr((unsigned long long *)&p.srcflag[s >> 6], 1ull << (s & 63));
                 }
-                const uint64_t qm = p.qmask[v];
+            }
+        }
+    }
+    for (int base = 0; base < na; base += 32) {
+        const bool valid = base + lane < na;
+        const int wv = wv_next;
+        wv_next = base + 32 + lane < na ? p.col[a0 + base + 32 + lane] : 0;
+        uint64_t nm[W];
+        bool any = false;
+        if (valid) {
+            const uint64_t *wrow = p.vs + (size_t)wv * stride;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                nm[w] = F[w] & ~(wrow[w] | wrow[cur * W + w]);
+                any |= nm[w] != 0ull;
+            }
+            if (MODE != kModeReach) {
+                st.arcs += 1;
+#pragma unroll
+                for (int w = 0; w < W; ++w) st.tight += (unsigned)__popcll(nm[w]);
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) nm[w] = 0ull;
+        }
+        // heads with new sources: mark them for the next level and claim
+        // the level's entry; the claim's answer (and the row bounds) are
+        // used only after the sigma adds, so their round trips overlap
+        int old = 0x7fffffff;
+        long long wrb = 0, wre = 0, wirb = 0, wire = 0;
+        if (any) {
+            uint64_t *wrow = p.vs + (size_t)wv * stride;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if (nm[w]) atomicOr((unsigned long long *)&wrow[nxt * W + w], (unsigned long long)nm[w]);
+            old = atomicMax(&p.tag[wv], L + 1);
+            wrb = p.off[wv];
+            wre = p.off[wv + 1];
+            if (MODE == kModeSpd) {
+                wirb = p.roff[wv];
+                wire = p.roff[wv + 1];
+            }
+        }
+        if (MODE != kModeReach) {
+            // two tight heads per step: their shuffles and atomics overlap
+            unsigned bal = __ballot_sync(kFull, any);
+            while (bal) {
+                const int i0 = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int i1 = bal ? __ffs(bal) - 1 : -1;
+                if (bal) bal &= bal - 1;
+                const int j1 = i1 < 0 ? i0 : i1;
+                const int w0 = __shfl_sync(kFull, wv, i0);
+                const int w1 = __shfl_sync(kFull, wv, j1);
+                uint64_t n0[W], n1[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    n0[w] = __shfl_sync(kFull, nm[w], i0);
+                    n1[w] = __shfl_sync(kFull, nm[w], j1);
+                }
+                if (i1 < 0) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) n1[w] = 0ull;
+                }
+                double *r0 = p.sigma + (size_t)w0 * S;
+                double *r1 = p.sigma + (size_t)w1 * S;
 #pragma unroll
                 for (int ii = 0; ii < PL; ++ii) {
                     const int s = lane + 32 * ii;
-                    if (mask_bit<W>(F, s)) {
-                        if (qm) {
-                            uint64_t x = qm & s_need[s];
-                            while (x) {
-                                const int q = __ffsll((long long)x) - 1;
-                                x &= x - 1;
-                                p.qlevel[s * 64 + q] = L;
-                            }
-                        }
-                        if (sig[ii] >= 9007199254740992.0)
-                            atomicOr((unsigned long long *)&p.srcflag[s >> 6], 1ull << (s & 63));
-                    }
+                    if (mask_bit<W>(n0, s)) atomicAdd(&r0[s], sig[ii]);
+                    if (mask_bit<W>(n1, s)) atomicAdd(&r1[s], sig[ii]);
                 }
             }
         }
-        for (int base = 0; base < na; base += 32) {
-            const bool valid = base + lane < na;
-            const int wv = wv_next;
-            wv_next = base + 32 + lane < na ? p.col[a0 + base + 32 + lane] : 0;
-            uint64_t nm[W];
-            bool any = false;
-            if (valid) {
-                const uint64_t *wrow = p.vs + (size_t)wv * stride;
-#pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    nm[w] = F[w] & ~(wrow[w] | wrow[cur * W + w]);
-                    any |= nm[w] != 0ull;
-                }
-                if (MODE != kModeReach) {
-                    st.arcs += 1;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) st.tight += (unsigned)__popcll(nm[w]);
-                }
-            } else {
-#pragma unroll
-                for (int w = 0; w < W; ++w) nm[w] = 0ull;
+        const bool app = any && old < L + 1;
+        int wnch = 0, winch = 0;
+        if (app) {
+            wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
+            if (MODE == kModeSpd) winch = (int)((wire - wirb + CH - 1) / CH);
+            if (MODE != kModeReach && old < 0) {
+                st.vb += 1;
+                st.eb += (unsigned)(wre - wrb);
             }
-            // heads with new sources: mark them for the next level and claim
-            // the level's entry; the claim's answer (and the row bounds) are
-            // used only after the sigma adds, so their round trips overlap
-            int old = 0x7fffffff;
-            long long wrb = 0, wre = 0, wirb = 0, wire = 0;
-            if (any) {
-                uint64_t *wrow = p.vs + (size_t)wv * stride;
-#pragma unroll
-                for (int w = 0; w < W; ++w)
-                    if (nm[w]) atomicOr((unsigned long long *)&wrow[nxt * W + w], (unsigned long long)nm[w]);
-                old = atomicMax(&p.tag[wv], L + 1);
-                wrb = p.off[wv];
-                wre = p.off[wv + 1];
-                if (MODE == kModeSpd) {
-                    wirb = p.roff[wv];
-                    wire = p.roff[wv + 1];
-                }
-            }
-            if (MODE != kModeReach) {
-                // two tight heads per step: their shuffles and atomics overlap
-                unsigned bal = __ballot_sync(kFull, any);
-                while (bal) {
-                    const int i0 = __ffs(bal) - 1;
-                    bal &= bal - 1;
-                    const int i1 = bal ? __ffs(bal) - 1 : -1;
-                    if (bal) bal &= bal - 1;
-                    const int j1 = i1 < 0 ? i0 : i1;
-                    const int w0 = __shfl_sync(kFull, wv, i0);
-                    const int w1 = __shfl_sync(kFull, wv, j1);
-                    uint64_t n0[W], n1[W];
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        n0[w] = __shfl_sync(kFull, nm[w], i0);
-                        n1[w] = __shfl_sync(kFull, nm[w], j1);
-                    }
-                    if (i1 < 0) {
-#pragma unroll
-                        for (int w = 0; w < W; ++w) n1[w] = 0ull;
-                    }
-                    double *r0 = p.sigma + (size_t)w0 * S;
-                    double *r1 = p.sigma + (size_t)w1 * S;
-#pragma unroll
-                    for (int ii = 0; ii < PL; ++ii) {
-                        const int s = lane + 32 * ii;
-                        if (mask_bit<W>(n0, s)) atomicAdd(&r0[s], sig[ii]);
-                        if (mask_bit<W>(n1, s)) atomicAdd(&r1[s], sig[ii]);
-                    }
-                }
-            }
-            const bool app = any && old < L + 1;
-            int wnch = 0, winch = 0;
-            if (app) {
-                wnch = (int)max(1ll, (wre - wrb + CH - 1) / CH);
-                if (MODE == kModeSpd) winch = (int)((wire - wirb + CH - 1) / CH);
-                if (MODE != kModeReach && old < 0) {
-                    st.vb += 1;
-                    st.eb += (unsigned)(wre - wrb);
-                }
-            }
-            warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, winch, wirb, wire, es1, cs1, ics1, lane);
         }
+        warp_append<W, MODE>(p, L, app, wv, wnch, wrb, wre, winch, wirb, wire, es1, cs1, ics1, lane);
+    }
+}
+
+// Expansion of level L (forward pass, Section 2 / Section 4.1). A warp takes
+// the level's chunks from the dynamic hand-out. With PIPE (the one-block-per-
+// SM kernels, which have the registers) the loop runs three chunks deep: the
+// descriptor of chunk i + 2 and the frontier mask and first heads of chunk
+// i + 1 are in flight while chunk i expands, so a chunk starts with one round
+// trip (sigma and the heads' masks) instead of three.
+template <int W, int MODE, bool PIPE>
+__device__ void forward_level(const TravParams &p, int L, long long cs, long long ccnt, long long es1,
+                              long long cs1, long long ics1, Stats &st, const uint64_t *s_need,
+                              long long gwarp, long long nwarps) {
+    const int lane = threadIdx.x & 31;
+    const int cur = 1 + (L & 1);
+    const int stride = p.vs_stride;
+    ChunkGrabber grab(&p.lev_grab[L], ccnt, nwarps);
+    if (!PIPE) {
+        long long c;
+        while (grab.next(c, lane)) {
+            const Chunk ch = load_chunk(&p.chunks[cs + c]);
+            const int w0 = lane < ch.na ? p.col[ch.a0 + lane] : 0;
+            const uint64_t *vrow = p.vs + (size_t)ch.v * stride;
+            uint64_t F[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) F[w] = vrow[cur * W + w];
+            expand_chunk<W, MODE>(p, L, ch, F, w0, es1, cs1, ics1, st, s_need);
+        }
+        return;
+    }
+    Chunk d0{}, d1{};
+    long long c0 = 0, c1 = 0;
+    bool h0 = grab.next(c0, lane);
+    if (h0) d0 = load_chunk(&p.chunks[cs + c0]);
+    bool h1 = h0 && grab.next(c1, lane);
+    if (h1) d1 = load_chunk(&p.chunks[cs + c1]);
+    uint64_t F0[W];
+    int w0 = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) F0[w] = 0ull;
+    if (h0) {
+        const uint64_t *vrow = p.vs + (size_t)d0.v * stride;
+#pragma unroll
+        for (int w = 0; w < W; ++w) F0[w] = vrow[cur * W + w];
+        w0 = lane < d0.na ? p.col[d0.a0 + lane] : 0;
+    }
+    while (h0) {
+        // chunk i + 2: descriptor; chunk i + 1: frontier mask and first heads
+        Chunk d2{};
+        long long c2 = 0;
+        const bool h2 = h1 && grab.next(c2, lane);
+        if (h2) d2 = load_chunk(&p.chunks[cs + c2]);
+        uint64_t F1[W];
+        int w1 = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) F1[w] = 0ull;
+        if (h1) {
+            const uint64_t *vrow = p.vs + (size_t)d1.v * stride;
+#pragma unroll
+            for (int w = 0; w < W; ++w) F1[w] = vrow[cur * W + w];
+            w1 = lane < d1.na ? p.col[d1.a0 + lane] : 0;
+        }
+        expand_chunk<W, MODE>(p, L, d0, F0, w0, es1, cs1, ics1, st, s_need);
+        h0 = h1;
+        d0 = d1;
+#pragma unroll
+        for (int w = 0; w < W; ++w) F0[w] = F1[w];
+        w0 = w1;
+        h1 = h2;
+        d1 = d2;
     }
 }
 
@@ -955,11 +1024,15 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
         int L = 0;
         long long total = 0;
         for (;;) {
-            const long long ecnt = (long long)ld_vol(&p.lev_cnt[L]);
-            const long long ccnt = (long long)ld_vol(&p.lev_ccnt[L]);
+            // the level's entries and chunks, counted in one word by warp_append
+            const unsigned long long pk = ld_vol(&p.lev_grab[4 * ((long long)p.maxlev + 2) + L]);
+            const long long ecnt = (long long)(pk & 0xffffffffull);
+            const long long ccnt = (long long)(pk >> 32);
             const long long iccnt = (long long)ld_vol(&p.lev_grab[2 * ((long long)p.maxlev + 2) + L]);
             const long long es1 = es + ecnt, cs1 = cs + ccnt, ics1 = ics + iccnt;
             if (blockIdx.x == 0 && threadIdx.x == 0) {
+                p.lev_cnt[L] = (unsigned long long)ecnt;  // published for the passes after the forward
+                p.lev_ccnt[L] = (unsigned long long)ccnt;
                 p.lev_start[L] = es;
                 p.lev_cstart[L] = cs;
                 p.lev_start[L + 1] = es1;
@@ -985,11 +1058,11 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                 pull_level<W, MODE>(p, L, es, es1, cs1, ics1, st, s_need, s_valid, gwarp, nwarps);
                 if (timer) atomicAdd(&p.ctr->pull_levels, 1ull);
             } else {
-                forward_level<W, MODE>(p, L, cs, ccnt, es1, cs1, ics1, st, s_need, gwarp, nwarps);
+                forward_level<W, MODE, MINB == 1>(p, L, cs, ccnt, es1, cs1, ics1, st, s_need, gwarp, nwarps);
             }
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
             total = es1;
-            if (ld_vol(&p.lev_cnt[L + 1]) == 0ull) break;
+            if ((ld_vol(&p.lev_grab[4 * ((long long)p.maxlev + 2) + L + 1]) & 0xffffffffull) == 0ull) break;
             if (L + 2 > p.maxlev) {
                 if (threadIdx.x == 0) set_err(p.ctr, kDevLevelOverflow);
                 return;
@@ -1153,6 +1226,7 @@ __global__ void __launch_bounds__(512, MINB) trav_kernel(TravParams p) {
                     p.lev_grab[p.maxlev + 2 + l] = 0ull;
                     p.lev_grab[2 * (p.maxlev + 2) + l] = 0ull;
                     p.lev_grab[3 * (p.maxlev + 2) + l] = 0ull;
+                    p.lev_grab[4 * (p.maxlev + 2) + l] = 0ull;
                 }
             }
         }
