@@ -71,6 +71,8 @@ WORKLOADS = {
     "rmat22_ef8_recip30_sampled64": "R-MAT scale 22, edge factor 8, seed 22, 30% of arcs also reversed (seed 22), "
                                     "repeats removed; 64 uniform queries (seed 105), A-BCD eps 0.01 delta 0.1 "
                                     "(T = 14,979) Philox seed 7",
+    "rmat20_w255_exact32": "R-MAT scale 20, edge factor 16, seed 20, loops and repeats removed, arc weights uniform "
+                           "in 1..255 (uint32, seed 3); 32 exact queries, uniform (seed 104)",
 }
 
 
@@ -79,6 +81,11 @@ def make_workload(name=WORKLOAD):
     if name == "rmat20_ef16_exact64":
         g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
         qs = [int(x) for x in gg.random_vertices(g.n, 32, 103)] + [int(x) for x in gg.top_inout_vertices(g, 32)]
+        return g, qs, [{"r": r} for r in qs]
+    if name == "rmat20_w255_exact32":
+        g = gg.rmat(20, 16, 0.57, 0.19, 0.19, seed=20)
+        g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+        qs = [int(x) for x in gg.random_vertices(g.n, 32, 104)]
         return g, qs, [{"r": r} for r in qs]
     if name == "rmat22_ef8_recip30_sampled64":
         g = gg.add_reciprocal(gg.rmat(22, 8, seed=22), 0.3, seed=22)
@@ -265,15 +272,18 @@ def solve_step(bcd, dg, specs, rank, world, dist):
     return tot, box["info"], box["out"]
 
 
-def algorithmic_bytes(info):
+def algorithmic_bytes(info, weighted=False):
     """The traversal's algorithmic bytes (see the design notes): graph
-    structure 2 (8 |V_B| + 4 |E_B|) summed over tiles; the forward pass, 24
-    bytes per reached (source, vertex) pair (level and sigma written and read
-    back) and 8 per tight (source, arc) pair (sigma of the tail); the Eq. 4
-    backward, on the tiles that ran it, 16 more per reached pair (delta
-    written and read) and 16 per tight pair (sigma and delta of the head);
-    the vertex scan, 16 per term (sigma_st and sigma_rt)."""
-    return (2.0 * (8.0 * info["union_vertices"] + 4.0 * info["union_arcs"]) + 24.0 * info["reached_pairs"] +
+    structure 2 (8 |V_B| + 4 |E_B|) summed over tiles (8 bytes per arc with
+    its weight); the forward pass, 24 bytes per reached (source, vertex) pair
+    (level and sigma written and read back; 32 with 8-byte distances) and 8
+    per tight (source, arc) pair (sigma of the tail); the Eq. 4 backward, on
+    the tiles that ran it, 16 more per reached pair (delta written and read)
+    and 16 per tight pair (sigma and delta of the head); the vertex scan, 16
+    per term (sigma_st and sigma_rt)."""
+    arc = 8.0 if weighted else 4.0
+    pair = 32.0 if weighted else 24.0
+    return (2.0 * (8.0 * info["union_vertices"] + arc * info["union_arcs"]) + pair * info["reached_pairs"] +
             8.0 * info["tight_pairs"] + 16.0 * info["eq4_reached_pairs"] + 16.0 * info["eq4_tight_pairs"] +
             16.0 * info["scan_pairs"])
 
@@ -311,8 +321,9 @@ def run_gpu(args):
         cpu_thread = threading.Thread(target=cpu_job, daemon=True)
         cpu_thread.start()
     stream = torch.cuda.Stream()
-    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, stream=stream.cuda_stream)
-    bcd.bc_set_config(dg, tile_words=args.tile_words)
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights, stream=stream.cuda_stream)
+    if g.weights is None:
+        bcd.bc_set_config(dg, tile_words=args.tile_words)
 
     def barrier():
         torch.cuda.synchronize()
@@ -343,26 +354,29 @@ def run_gpu(args):
     gteps = sum_over_ranks(edges, dist if world > 1 else None) / (ms / 1000.0) / 1e9
     trav_ms = float(np.mean([i["ms_traversal"] for i in infos]))
     launches = int(sum(i["launches"] for i in infos) / args.steps)
-    algo_bytes = float(np.mean([algorithmic_bytes(i) for i in infos]))
+    algo_bytes = float(np.mean([algorithmic_bytes(i, g.weights is not None) for i in infos]))
     peak, peak_kind = peaks()
     achieved = algo_bytes / (trav_ms / 1000.0) / 1e9
     traffic = None
     if (TRAFFIC["bytes_per_reached_arc"] and TRAFFIC["sources_sha256"] == kernel_sha() and
-            args.tile_words == TRAFFIC["tile_words"]):
+            args.tile_words == TRAFFIC["tile_words"] and g.weights is None):
         traffic = TRAFFIC["bytes_per_reached_arc"] * edges
 
     # end to end through the C ABI: pinned host CSR in, results out
     off_h = torch.from_numpy(g.offsets).pin_memory()
     col_h = torch.from_numpy(g.cols).pin_memory()
+    w_h = None if g.weights is None else torch.from_numpy(g.weights.view(np.int32)).pin_memory()
     barrier()
     t = time.time()
-    ge = bcd.bc_graph_create(g.n, off_h.numpy(), col_h.numpy(), stream=stream.cuda_stream)
-    bcd.bc_set_config(ge, tile_words=args.tile_words)
+    ge = bcd.bc_graph_create(g.n, off_h.numpy(), col_h.numpy(), None if w_h is None else w_h.numpy().view(np.uint32),
+                             stream=stream.cuda_stream)
+    if g.weights is None:
+        bcd.bc_set_config(ge, tile_words=args.tile_words)
     scores_e, _, _ = solve_step(bcd, ge, specs, rank, world, dist)
     ge.close()
     barrier()
     e2e_s = max_over_ranks(time.time() - t, dist if world > 1 else None)
-    h2d = g.offsets.nbytes + g.cols.nbytes + nq * 40
+    h2d = g.offsets.nbytes + g.cols.nbytes + (0 if g.weights is None else g.weights.nbytes) + nq * 40
     d2h = nq * 32
 
     extras = {}
@@ -400,7 +414,8 @@ def run_gpu(args):
                           "backward": float(np.mean([i["ms_backward"] for i in infos]))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "trav_kernel (batched SPD + dependency traversal)",
+                         "kernel": ("wtrav_kernel (weighted batched SPD + dependencies)" if g.weights is not None
+                                    else "trav_kernel (batched SPD + dependency traversal)"),
                          "algorithmic_bytes": algo_bytes},
             "e2e": {"value": job_rate(nq, 1000.0 * e2e_s), "unit": "queries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -606,6 +621,43 @@ def run_serve(args):
     dg.close()
 
 
+def run_error_vs_exact(args):
+    """The sampled batch against the exact scores of its query vertices: the
+    64 uniform queries of the R-MAT 22 workload, A-BCD (eps 0.01, delta 0.1,
+    Philox seed 7) and E-BCD in one bc_batch each, and per query the paper's
+    error 100 |App - BC| / BC (Section 5), with the distribution over the
+    queries whose exact score is not 0."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_08739_gb300 as bcd
+    g, qs, specs = make_workload("rmat22_ef8_recip30_sampled64")
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
+    t = time.time()
+    app, ai = bcd.bc_batch(dg, specs)
+    t_app = time.time() - t
+    t = time.time()
+    ex, ei = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    t_ex = time.time() - t
+    rows = []
+    for r, a, e in zip(qs, app, ex):
+        err = None if e["bc"] == 0.0 else 100.0 * abs(a["bc"] - e["bc"]) / e["bc"]
+        rows.append({"r": r, "rv_size": e["rv_size"], "exact": e["bc"], "sampled": a["bc"], "error_pct": err})
+    errs = sorted(x["error_pct"] for x in rows if x["error_pct"] is not None)
+    print(json.dumps({"experiment": "error_vs_exact", "workload": "rmat22_ef8_recip30_sampled64",
+                      "sampled_s": t_app, "exact_s": t_ex, "exact_sources": ei["sources_run"],
+                      "exact_tiles": ei["tiles"], "exact_scan_tiles": ei["scan_tiles"],
+                      "queries_nonzero": len(errs), "queries_zero_both": sum(1 for x in rows if x["exact"] == 0.0 and
+                                                                             x["sampled"] == 0.0),
+                      "error_pct": {"mean": float(np.mean(errs)) if errs else None,
+                                    "median": float(np.median(errs)) if errs else None,
+                                    "p90": float(np.percentile(errs, 90)) if errs else None,
+                                    "max": errs[-1] if errs else None},
+                      "rows": rows}), flush=True)
+    dg.close()
+
+
 def run_profile_case(args):
     """A small launch of the same traversal kernel for ncu captures: one
     sampled query (T = args.case_T draws, seed 7) on the R-MAT 20 graph, with
@@ -772,6 +824,8 @@ def main():
     ap.add_argument("--single", action="store_true",
                     help="single-query latency under both accumulations (Eq. 4 push, vertex scan)")
     ap.add_argument("--single-reps", type=int, default=5)
+    ap.add_argument("--error-vs-exact", action="store_true",
+                    help="the R-MAT 22 sampled batch against the exact scores of its 64 query vertices")
     ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2],
                     help="profile / wprofile cases: 1 Eq. 4 backward (their default), 2 vertex scan")
     ap.add_argument("--serve-queries", type=int, default=10000)
@@ -784,6 +838,8 @@ def main():
         args.warmup = 3
     if args.serve:
         run_serve(args)
+    elif args.error_vs_exact:
+        run_error_vs_exact(args)
     elif args.single:
         run_single(args)
     elif args.set_experiment:

@@ -153,9 +153,10 @@ struct TravParams {
     int32_t pad3;
     const int32_t *qcol;     // [64]
     const int32_t *croot;    // [64]
-    int32_t *rlevq;          // [n * 64], -1 unreached
+    int32_t *rlevq;          // [n * 64], -1 unreached (unweighted)
+    uint64_t *rdistq;        // [n * 64], UINT64_MAX unreached (weighted)
     double *rsigq;           // [n * 64]
-    double *msum;            // [S * 64]
+    double *msum;            // [2 * S * 64]: sums, then (weighted) sigma_s(croot[c])
     // reach mode output
     uint64_t *rvmask;        // [n]
     int32_t *levout;         // [n] level of first discovery (reach mode, one root), or NULL
@@ -225,6 +226,7 @@ struct bcd_workspace {
     double *rsig = nullptr;       // [n] ... and its path counts
     double *vsum = nullptr;       // [2 * 64 * W] ... and the per-source sums of a tile
     int32_t *rlevq = nullptr;     // [n * 64] several query vertices: levels from each (unweighted graphs)
+    uint64_t *rdistq = nullptr;   // [n * 64] ... distances from each (weighted graphs)
     double *rsigq = nullptr;      // [n * 64] ... and path counts
     double *msum = nullptr;       // [64 * W * 64] per-(source, column) sums of a tile
     int32_t *rtile = nullptr;     // [64 * W] the one-source tile of the query vertex's traversal

@@ -360,6 +360,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.rsig);
     dev_free(ws.vsum);
     dev_free(ws.rlevq);
+    dev_free(ws.rdistq);
     dev_free(ws.rsigq);
     dev_free(ws.msum);
     dev_free(ws.rtile);
@@ -423,7 +424,7 @@ static bc_status build_workspace(bc_graph *g, int W) {
         BCD_TRY(dev_alloc(&ws.rlev, (size_t)n));
     BCD_TRY(dev_alloc(&ws.rsig, (size_t)n));
     BCD_TRY(dev_alloc(&ws.vsum, (size_t)2 * 64 * W));
-    BCD_TRY(dev_alloc(&ws.msum, (size_t)64 * W * 64));
+    BCD_TRY(dev_alloc(&ws.msum, (size_t)2 * 64 * W * 64));
     BCD_TRY(dev_alloc(&ws.rtile, (size_t)64 * W));
     BCD_TRY(dev_alloc(&ws.qflags, 64));
     BCD_TRY(dev_alloc(&ws.srcflag, (size_t)std::max(W, 4)));
@@ -706,7 +707,7 @@ static bc_status root_traversal(bc_graph *g, int32_t r) {
 // 64 vertices (accumulation 3).
 static bool use_vertex_scan(const bc_graph *g, size_t nroots) {
     if (nroots == 1) return g->accumulation >= 2;
-    return g->accumulation >= 3 && !g->weighted && nroots <= 64;
+    return g->accumulation >= 3 && nroots <= 64;
 }
 
 // Cost of one term of the vertex scan (a division and a shared-memory add,
@@ -729,15 +730,22 @@ static bc_status root_traversal_multi(bc_graph *g, const std::vector<int32_t> &r
     const int W = tile_words_of(g);
     const int S = 64 * W;
     const int K = (int)roots.size();
-    if (!ws.rlevq) {
-        BCD_TRY(dev_alloc(&ws.rlevq, (size_t)g->n * 64));
+    if (!ws.rsigq) {
+        if (g->weighted)
+            BCD_TRY(dev_alloc(&ws.rdistq, (size_t)g->n * 64));
+        else
+            BCD_TRY(dev_alloc(&ws.rlevq, (size_t)g->n * 64));
         bc_status st = dev_alloc(&ws.rsigq, (size_t)g->n * 64);
         if (st != BC_OK) {
             dev_free(ws.rlevq);
+            dev_free(ws.rdistq);
             return st;
         }
     }
-    BCD_CUDA(cudaMemsetAsync(ws.rlevq, 0xff, sizeof(int32_t) * (size_t)g->n * 64, s));
+    if (g->weighted)
+        BCD_CUDA(cudaMemsetAsync(ws.rdistq, 0xff, sizeof(uint64_t) * (size_t)g->n * 64, s));
+    else
+        BCD_CUDA(cudaMemsetAsync(ws.rlevq, 0xff, sizeof(int32_t) * (size_t)g->n * 64, s));
     std::vector<int32_t> tsrc(S, -1);
     for (int c = 0; c < K; ++c) tsrc[c] = roots[c];
     BCD_CUDA(cudaMemcpyAsync(ws.rtile, tsrc.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
@@ -766,6 +774,7 @@ static bc_status root_traversal_multi(bc_graph *g, const std::vector<int32_t> &r
     p.qcol = (const int32_t *)(ws.small + kSmallQcol);  // uploaded by the caller
     p.croot = (const int32_t *)(ws.small + kSmallCroot);
     p.rlevq = ws.rlevq;
+    p.rdistq = ws.rdistq;
     p.rsigq = ws.rsigq;
     p.msum = ws.msum;
     p.vroot = roots[0];
@@ -794,11 +803,11 @@ static bc_status scan_roots(bc_graph *g, const std::vector<int32_t> &roots, cons
         for (size_t c = 0; c < roots.size(); ++c) croot[c] = roots[c];
         BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallQcol, qcol.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         BCD_CUDA(cudaMemcpyAsync(ws.small + kSmallCroot, croot.data(), 64 * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        if (g->root_cache == roots && ws.rlevq && g->root_cache_buf == (const void *)ws.rlevq) return BC_OK;
+        if (g->root_cache == roots && ws.rsigq && g->root_cache_buf == (const void *)ws.rsigq) return BC_OK;
         g->root_cache.clear();
         BCD_TRY(root_traversal_multi(g, roots));
         g->root_cache = roots;
-        g->root_cache_buf = ws.rlevq;
+        g->root_cache_buf = ws.rsigq;
     } else {
         const void *buf = g->weighted ? (const void *)ws.rdist : (const void *)ws.rlev;
         if (g->root_cache == roots && g->root_cache_buf == buf) return BC_OK;
@@ -972,6 +981,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
                 p.qcol = (const int32_t *)(ws.small + kSmallQcol);
                 p.croot = (const int32_t *)(ws.small + kSmallCroot);
                 p.rlevq = ws.rlevq;
+                p.rdistq = ws.rdistq;
                 p.rsigq = ws.rsigq;
                 p.msum = ws.msum;
             }
@@ -1233,6 +1243,7 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
             p.qcol = (const int32_t *)(ws.small + kSmallQcol);
             p.croot = (const int32_t *)(ws.small + kSmallCroot);
             p.rlevq = ws.rlevq;
+            p.rdistq = ws.rdistq;
             p.rsigq = ws.rsigq;
             p.msum = ws.msum;
         }

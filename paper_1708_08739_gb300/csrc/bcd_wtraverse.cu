@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
             for (int i = threadIdx.x; i < p.nw; i += blockDim.x) p.srcflag[i] = 0ull;
             if (p.mode == kModeScan)
                 for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) p.vsum[i] = 0.0;
+            if (p.mode == kModeScan && p.ncols >= 2)
+                for (int i = threadIdx.x; i < S * 64; i += blockDim.x) p.msum[i] = 0.0;
         }
         for (int s = threadIdx.x; s < S; s += blockDim.x) {
             const int32_t v = tsrc[s];
@@ -424,13 +426,70 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
 
         // ---------------- the query vertex's own traversal ----------------
         if (p.mode == kModeScan && (p.flags & kFlagRootOut)) {
-            // source slot 0 is r: keep d(r, t) and sigma_rt
+            // source slot 0 is r: keep d(r, t) and sigma_rt; with several query
+            // vertices, slot c is column c
             for (long long e = gthr; e < total; e += nthr) {
                 const int v = p.hv[e];
-                const size_t iv = ((size_t)v << tl.shift) + p.hs[e];
-                p.rdist[v] = p.dist[iv];
-                p.rsig[v] = p.sigma[iv];
+                const int c = p.hs[e];
+                const size_t iv = ((size_t)v << tl.shift) + c;
+                if (p.ncols >= 2) {
+                    p.rdistq[(size_t)v * 64 + c] = p.dist[iv];
+                    p.rsigq[(size_t)v * 64 + c] = p.sigma[iv];
+                } else {
+                    p.rdist[v] = p.dist[iv];
+                    p.rsig[v] = p.sigma[iv];
+                }
             }
+            if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
+        }
+        // ---------------- vertex scan, several query vertices ----------------
+        // Column c (query vertex r_c) of a settled pair (t, s) of distance D
+        // takes sigma_{r_c t} / sigma_st when d(s, r_c) + d(r_c, t) = D with
+        // d(r_c, t) >= 1, for the columns of the queries that need s; the terms
+        // meet in msum[s * 64 + c] by fp64 atomic adds. Block 0 keeps
+        // sigma_s(r_c) in msum[S * 64 + s * 64 + c] before the closing barrier
+        // (the tile-end reset clears sigma).
+        if (p.mode == kModeScan && p.ncols >= 2 && !(p.flags & (kFlagRootOut | kFlagNoBackward))) {
+            unsigned pairs = 0;
+            for (int sg = 1; sg < nseg; ++sg) {
+                const long long e0 = p.lev_start[sg];
+                const long long ne = (long long)p.lev_cnt[sg];
+                const unsigned long long dk = (unsigned long long)p.lev_dist[sg];
+                for (long long i = gthr; i < ne; i += nthr) {
+                    const long long e = e0 + i;
+                    const int t = p.hv[e];
+                    const int s = p.hs[e];
+                    uint64_t x = s_need[s];
+                    uint64_t done = 0ull;
+                    double sst = 0.0;
+                    while (x) {
+                        const int q = __ffsll((long long)x) - 1;
+                        x &= x - 1;
+                        const int c = p.qcol[q];
+                        if ((done >> c) & 1ull) continue;
+                        done |= 1ull << c;
+                        const int ql = p.qlevel[s * 64 + q];
+                        if (ql < 0) continue;
+                        const unsigned long long rd = p.rdistq[(size_t)t * 64 + c];
+                        if (rd == 0ull || rd >= dk) continue;  // t = r_c, unreached from r_c, or too far
+                        if ((unsigned long long)p.lev_dist[ql] + rd != dk) continue;
+                        if (sst == 0.0) sst = p.sigma[((size_t)t << tl.shift) + s];
+                        atomicAdd(&p.msum[s * 64 + c], p.rsigq[(size_t)t * 64 + c] / sst);
+                        ++pairs;
+                    }
+                }
+            }
+            if (blockIdx.x == 0) {
+                for (int i = threadIdx.x; i < S * 64; i += blockDim.x) {
+                    const int s = i >> 6, q = i & 63;
+                    if (!((s_need[s] >> q) & 1ull)) continue;
+                    const int c = p.qcol[q];
+                    p.msum[(size_t)S * 64 + s * 64 + c] = p.sigma[((size_t)p.croot[c] << tl.shift) + s];
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+            if (lane == 0 && pairs) atomicAdd(&p.ctr->vpairs, (unsigned long long)pairs);
             if (!grid_barrier(p.ctr, gen, p.timeout_ns)) return;
         }
         // ---------------- vertex scan over the settled pairs ----------------
@@ -439,7 +498,7 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
         // (t != r). d(s, r) is the distance of the level at which r settled
         // for s (its query level). Terms meet in vsum[s] by fp64 atomic adds;
         // block 0 keeps sigma_sr in vsum[S + s] before the closing barrier.
-        if (p.mode == kModeScan && !(p.flags & (kFlagRootOut | kFlagNoBackward))) {
+        if (p.mode == kModeScan && p.ncols < 2 && !(p.flags & (kFlagRootOut | kFlagNoBackward))) {
             for (int s = threadIdx.x; s < S; s += blockDim.x) {
                 const uint64_t x = s_need[s];
                 const int qs = x ? p.qlevel[s * 64 + __ffsll((long long)x) - 1] : -1;
@@ -566,14 +625,19 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
 
         // ---------------- tile end ----------------
         if (p.mode == kModeScan && blockIdx.x == 0) {
-            // every query of a scan launch has the same vertex: one value per source
+            // one value per source (one query vertex) or per (source, column)
             for (int s = threadIdx.x; s < S; s += blockDim.x) {
                 uint64_t x = s_need[s];
                 const double dv = p.vsum[S + s] * p.vsum[s];
                 while (x) {
                     const int q = __ffsll((long long)x) - 1;
                     x &= x - 1;
-                    p.dep[s * 64 + q] = dv;
+                    if (p.ncols >= 2) {
+                        const int c = p.qcol[q];
+                        p.dep[s * 64 + q] = p.msum[(size_t)S * 64 + s * 64 + c] * p.msum[s * 64 + c];
+                    } else {
+                        p.dep[s * 64 + q] = dv;
+                    }
                 }
             }
             __syncthreads();

@@ -411,19 +411,28 @@ def test_multi_vertex_scan_edge_cases(bcd, sparse_er):
         assert close(o["bc"], O.bc_exact(ogd, r, 0)[0]), r
 
 
-def test_multi_vertex_scan_weighted_keeps_eq4(bcd):
-    """On a weighted graph accumulation 3 keeps the one-vertex scan for
-    one-vertex groups and Eq. 4 for the others; results match the oracle."""
+@pytest.mark.parametrize("cfg", [{}, {"weighted_words": 1}, {"weighted_words": 2, "chunk_arcs": 32}])
+@pytest.mark.parametrize("wmax", [255, 3])
+def test_multi_vertex_scan_weighted(bcd, cfg, wmax):
+    """Weighted graphs (weights 1..255, and 1..3 with many equal-length
+    paths): a group at 10 distinct vertices (repeats and a sampled query
+    among them) takes the vertex scan over settled (vertex, source) pairs
+    with accumulation 3 and matches the oracle."""
     g = gg.erdos_renyi(600, 4000, 21)
-    g = g.with_weights(gg.uniform_weights(g.m, 1, 3, 4))
+    g = g.with_weights(gg.uniform_weights(g.m, 1, wmax, 4))
     og = O.Graph.from_csr(g)
-    dg = make(bcd, g)
+    dg = make(bcd, g, **cfg)
     bcd.bc_set_config(dg, accumulation=3)
-    rs = gg.random_vertices(g.n, 6, 64).tolist()
-    out, info = bcd.bc_batch(dg, [{"r": r} for r in rs])
-    assert info["scan_pairs"] == 0
-    for r, o in zip(rs, out):
-        assert close(o["bc"], O.bc_exact(og, r, 0)[0]), r
+    rs = gg.random_vertices(g.n, 10, 64).tolist()
+    specs = [{"r": r} for r in rs] + [{"r": rs[0]}, {"r": rs[1], "kind": bcd.BC_QUERY_APPROX_T, "T": 200, "seed": 7}]
+    out, info = bcd.bc_batch(dg, specs)
+    assert info["scan_pairs"] > 0
+    for sp, o in zip(specs, out):
+        if sp.get("kind", 0) == 0:
+            want = O.bc_exact(og, sp["r"], 0)[0]
+        else:
+            want = O.bc_approx(og, sp["r"], 200, 7, 0)[0]
+        assert o["status"] == 0 and close(o["bc"], want), (cfg, sp, o["bc"], want)
 
 
 def test_auto_choice_per_group(bcd, er1):
