@@ -659,20 +659,34 @@ def run_error_vs_exact(args):
 
 
 def run_profile_case(args):
-    """A small launch of the same traversal kernel for ncu captures: one
-    sampled query (T = args.case_T draws, seed 7) on the R-MAT 20 graph, with
-    the Eq. 4 backward of the batched kernel (--accumulation 2: the vertex
-    scan)."""
+    """A small launch of the same traversal kernel for ncu captures, on the
+    R-MAT 20 graph: one sampled query (T = args.case_T draws, seed 7) at the
+    vertex of largest in-degree x out-degree, or with --case-queries k > 1,
+    k uniform queries from the giant component (seed 103) with T = args.case_T
+    / k draws each (seeds 7, 8, ...), as in the bench's batch of many query
+    vertices. --accumulation picks the backward (default 1: Eq. 4)."""
     import __graft_entry__
     __graft_entry__.build()
     import paper_1708_08739_gb300 as bcd
     g, qs, _ = make_workload("rmat20_ef16_exact64")
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)
     bcd.bc_set_config(dg, tile_words=args.tile_words, accumulation=args.accumulation or 1)
-    r = int(gg.top_inout_vertices(g, 1)[0])
-    out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
-    print(json.dumps({"case": "profile", "r": r, "T": args.case_T, "bc": out[0]["bc"],
-                      "accumulation": bcd.bc_get_config(dg)["accumulation"], "info": info}), flush=True)
+    if args.case_queries <= 1:
+        r = int(gg.top_inout_vertices(g, 1)[0])
+        specs = [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}]
+    else:
+        pick = []
+        for r in qs[:32]:
+            if g.out_degree()[r] > 0 and r not in pick and bcd.bc_rv_compute(dg, r).shape[0] > 1000:
+                pick.append(r)
+            if len(pick) == args.case_queries:
+                break
+        specs = [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T // len(pick), "seed": 7 + i}
+                 for i, r in enumerate(pick)]
+    out, info = bcd.bc_batch(dg, specs)
+    print(json.dumps({"case": "profile", "queries": [s["r"] for s in specs], "T": [s["T"] for s in specs],
+                      "bc": [o["bc"] for o in out], "accumulation": bcd.bc_get_config(dg)["accumulation"],
+                      "info": info}), flush=True)
     dg.close()
 
 
@@ -818,6 +832,7 @@ def main():
     ap.add_argument("--weighted-words", type=int, default=0, help="weighted tile width (64-source words; 0: default)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--case-T", type=int, default=512)
+    ap.add_argument("--case-queries", type=int, default=1, help="profile case: query vertices (1: the top vertex)")
     ap.add_argument("--serve", action="store_true", help="serving benchmark (continuous batching, p50/p99)")
     ap.add_argument("--set-experiment", action="store_true",
                     help="the set experiment of Section 5 (sets of 5, 10, 15 vertices, tau = 1000)")
@@ -826,8 +841,9 @@ def main():
     ap.add_argument("--single-reps", type=int, default=5)
     ap.add_argument("--error-vs-exact", action="store_true",
                     help="the R-MAT 22 sampled batch against the exact scores of its 64 query vertices")
-    ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2],
-                    help="profile / wprofile cases: 1 Eq. 4 backward (their default), 2 vertex scan")
+    ap.add_argument("--accumulation", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="profile / wprofile cases: 1 Eq. 4 backward (their default), 2 vertex scan, 3 scan over "
+                         "several vertices, 4 chosen per group")
     ap.add_argument("--serve-queries", type=int, default=10000)
     ap.add_argument("--serve-rates", default="0.5,0.8,1.0", help="Poisson arrival rates as fractions of saturation")
     ap.add_argument("--serve-single", type=int, default=256, help="queries run one at a time for the comparison")
