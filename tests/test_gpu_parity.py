@@ -427,6 +427,7 @@ def test_batch_shards_add_up(bcd, er1, nshards):
 
 @pytest.mark.parametrize("cfg", [{"pull_permille": 1}, {"pull_permille": 1, "tile_words": 1},
                                  {"pull_permille": 1, "tile_words": 2, "chunk_arcs": 32},
+                                 {"pull_permille": 1, "tile_words": 4, "blocks_per_sm": 1},
                                  {"pull_permille": 50}])
 def test_bottom_up_levels_bit_exact(bcd, er1, cfg):
     """Forward levels run bottom-up (every level from 1 on with 1 permille):
