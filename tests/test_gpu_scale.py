@@ -287,6 +287,28 @@ def test_rmat20_weighted_vertex_scan(bcd, rmat20w):
     assert close(scan[0]["bc"], want) and close(push[0]["bc"], want), (scan[0]["bc"], push[0]["bc"], want)
 
 
+def test_rmat20_weighted_multi_vertex_scan(bcd, rmat20w):
+    """The weighted batch's query vertices in the giant component (seed 104)
+    as one group under the default per-group choice (the vertex scan over
+    several vertices on the first tile, then the cheaper backward), A-BCD
+    with 32 draws each and its own seed, against the oracle's A-BCD on the
+    same draws."""
+    g, og, dg, qs = rmat20w
+    big = [r for r in dict.fromkeys(qs) if g.out_degree()[r] > 0 and bcd.bc_rv_compute(dg, r).shape[0] > 1000][:6]
+    assert len(big) >= 4
+    specs = [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 32, "seed": 11 + i} for i, r in enumerate(big)]
+    bcd.bc_set_config(dg, accumulation=4)
+    try:
+        out, info = bcd.bc_batch(dg, specs)
+    finally:
+        bcd.bc_set_config(dg, accumulation=1)
+    assert info["scan_tiles"] >= 1
+    threads = os.cpu_count() or 1
+    for s, o in zip(specs, out):
+        want = O.bc_approx(og, s["r"], 32, s["seed"], threads)[0]
+        assert o["status"] == 0 and close(o["bc"], want), (s, o["bc"], want)
+
+
 def test_rmat20_weighted_empty_rv_queries(bcd, rmat20w):
     """The queries outside the giant component have no in-arcs here: RV is
     empty and BC(r) = 0 (Prop. 1); the oracle agrees on each."""

@@ -161,3 +161,38 @@ def test_shard_split_and_assignment():
     assert sh.shards_of(0, 4, [0, 2]) == [0, 1]
     with pytest.raises(ValueError):
         sh.reduce_in_shard_order({0: [1.0]}, 2, 1)
+
+
+class FakeLib:
+    """Stands in for the CUDA binding in bench.solve_step: shard k of a
+    batch answers (k + 1) * 10^-3 * (query index + 1) for every query."""
+
+    def bc_batch(self, dg, specs):
+        raise AssertionError("a sharded step must not run the whole batch")
+
+    def bc_batch_shard(self, dg, specs, k, n):
+        out = [{"bc": (k + 1) * 1e-3 * (i + 1), "status": 0, "flags": 0, "rv_size": 1, "samples": 0}
+               for i in range(len(specs))]
+        return out, {"shard": k}
+
+
+def step_worker(rank, world, port, out):
+    init(rank, world, port)
+    import bench
+    tot, info, res = bench.solve_step(FakeLib(), None, [{"r": 0}, {"r": 1}, {"r": 2}], rank, world, dist)
+    out[rank] = (tot.tolist(), info["shard"])
+    dist.destroy_process_group()
+
+
+def test_bench_step_shards_and_sums():
+    """bench.solve_step under two ranks: each runs its own shard and every
+    rank ends with the shard-order sums of all shards."""
+    port = free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(step_worker, args=(2, port, out), nprocs=2, join=True)
+    want = [(1e-3 + 2e-3) * (i + 1) for i in range(3)]
+    for r in (0, 1):
+        tot, shard = out[r]
+        assert shard == r
+        assert all(abs(a - b) <= 1e-15 for a, b in zip(tot, want)), (tot, want)
