@@ -819,7 +819,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--tile-words", type=int, default=4)
+    ap.add_argument("--tile-words", type=int, default=4, help="64-source mask words per tile (1, 2, 4 or 8)")
     ap.add_argument("--cpu-budget-s", type=float, default=24.0,
                     help="seconds of oracle work for the all-core CPU baseline (a third of it single-threaded)")
     ap.add_argument("--ref-step-s", type=float, default=5.0, help="--impl reference: seconds of oracle work per step")

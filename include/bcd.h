@@ -318,10 +318,11 @@ void bc_server_destroy(bc_server *srv);
 /*
  * Tuning of the batched traversal (no effect on results beyond fp64
  * summation order of delta):
- *   tile_words     mask words per tile: 1, 2 or 4 (64, 128 or 256 sources
- *                  advanced together; bc_graph_create picks the widest
- *                  whose sigma and accumulator slabs, 16 bytes per (vertex,
- *                  source) pair, fit in half of the free device memory);
+ *   tile_words     mask words per tile: 1, 2, 4 or 8 (64, 128, 256 or 512
+ *                  sources advanced together; bc_graph_create picks the
+ *                  widest of 1, 2 and 4 whose sigma and accumulator slabs,
+ *                  16 bytes per (vertex, source) pair, fit in half of the
+ *                  free device memory; 8 runs one block per SM);
  *   chunk_arcs     arcs per unit of work when a vertex's row is split
  *                  (32..65536, a multiple of 32);
  *   block_threads  threads per block of the persistent kernel (128..512,
@@ -419,7 +420,7 @@ bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
  * current configuration, one parameter at a time takes each of its
  * candidate values with the others fixed, and the fastest (CUDA-event time
  * of the batch, second of two runs) is kept:
- *   unweighted: tile_words 2, 4; blocks_per_sm 1, 2; chunk_arcs 64, 128, 256;
+ *   unweighted: tile_words 2, 4, 8; blocks_per_sm 1, 2; chunk_arcs 64, 128, 256;
  *               pull_permille -1, 200; accumulation 1, 4;
  *   weighted:   weighted_words 2, 4, 8; weighted_short_row 16, 32, 64;
  *               chunk_arcs 64, 128, 256; accumulation 1, 4.

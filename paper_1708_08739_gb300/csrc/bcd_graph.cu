@@ -141,8 +141,8 @@ bc_status bc_set_stream(bc_graph *g, void *stream) {
 
 bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (!g || !c) return set_error(BC_E_INVALID_ARG, "bc_set_config: NULL argument");
-    if (c->tile_words && c->tile_words != 1 && c->tile_words != 2 && c->tile_words != 4)
-        return set_error(BC_E_INVALID_ARG, "bc_set_config: tile_words must be 1, 2 or 4");
+    if (c->tile_words && c->tile_words != 1 && c->tile_words != 2 && c->tile_words != 4 && c->tile_words != 8)
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: tile_words must be 1, 2, 4 or 8");
     if (c->chunk_arcs && (c->chunk_arcs < 32 || c->chunk_arcs > 65536 || c->chunk_arcs % 32))
         return set_error(BC_E_INVALID_ARG, "bc_set_config: chunk_arcs must be a multiple of 32 in [32, 65536]");
     if (c->block_threads && (c->block_threads < 128 || c->block_threads > 512 || c->block_threads % 32))

@@ -1590,7 +1590,7 @@ bc_status bc_tune(bc_graph *g, const bc_query *queries, int64_t nq, int64_t prob
         space.push_back({&bc_config::chunk_arcs, {64, 128, 256}});
         space.push_back({&bc_config::accumulation, {1, 4}});
     } else {
-        space.push_back({&bc_config::tile_words, {2, 4}});
+        space.push_back({&bc_config::tile_words, {2, 4, 8}});
         space.push_back({&bc_config::blocks_per_sm, {1, 2}});
         space.push_back({&bc_config::chunk_arcs, {64, 128, 256}});
         space.push_back({&bc_config::pull_permille, {-1, 200}});

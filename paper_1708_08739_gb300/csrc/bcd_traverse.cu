@@ -860,7 +860,7 @@ __device__ __noinline__ void vertex_scan_multi(const TravParams &p, int Lmax, co
                                                long long nwarps) {
     constexpr int S = 64 * W;
     constexpr int PL = 2 * W;
-    constexpr int G = 8;  // columns per pass
+    constexpr int G = W >= 8 ? 4 : 8;  // columns per pass (the shared sums of 512 sources x 8 columns would pass 48 KB)
     __shared__ double s_acc[S * G];
     __shared__ int32_t s_ql[S * G];  // d(s, r_c) for sources that need column c, else -1
     __shared__ int32_t s_kmin[G], s_kmax[G];
@@ -918,9 +918,14 @@ __device__ __noinline__ void vertex_scan_multi(const TravParams &p, int Lmax, co
                 if (e < eend) {
                     t = p.hv[e];
                     const int4 *row = reinterpret_cast<const int4 *>(p.rlevq + (size_t)t * 64 + cg);
-                    const int4 a = row[0], c = row[1];
-                    dr[0] = a.x; dr[1] = a.y; dr[2] = a.z; dr[3] = a.w;
-                    dr[4] = c.x; dr[5] = c.y; dr[6] = c.z; dr[7] = c.w;
+#pragma unroll
+                    for (int h = 0; h < G / 4; ++h) {
+                        const int4 a = row[h];
+                        dr[4 * h] = a.x;
+                        dr[4 * h + 1] = a.y;
+                        dr[4 * h + 2] = a.z;
+                        dr[4 * h + 3] = a.w;
+                    }
 #pragma unroll
                     for (int j = 0; j < G; ++j) {
                         const int k = L - dr[j];
@@ -1352,16 +1357,20 @@ bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsi
                 st = g->blocks_per_sm == 3 ? launch<2, kModeScan, 3>(g, p) : launch<2, kModeScan, 2>(g, p);
             else if (W == 4)
                 st = g->blocks_per_sm == 2 ? launch<4, kModeScan, 2>(g, p) : launch<4, kModeScan, 1>(g, p);
+            else if (W == 8)
+                st = launch<8, kModeScan, 1>(g, p);
             else
-                return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
+                return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2, 4 or 8");
         } else if (W == 1) {
             st = launch<1, kModeSpd, 2>(g, p);
         } else if (W == 2) {
             st = g->blocks_per_sm == 3 ? launch<2, kModeSpd, 3>(g, p) : launch<2, kModeSpd, 2>(g, p);
         } else if (W == 4) {
             st = g->blocks_per_sm == 2 ? launch<4, kModeSpd, 2>(g, p) : launch<4, kModeSpd, 1>(g, p);
+        } else if (W == 8) {
+            st = launch<8, kModeSpd, 1>(g, p);
         } else {
-            return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2 or 4");
+            return set_error(BC_E_INVALID_ARG, "tile words must be 1, 2, 4 or 8");
         }
         if (timed) cudaEventRecord(ev1, g->stream);
         if (st != BC_OK) {

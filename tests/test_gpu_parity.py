@@ -63,7 +63,7 @@ def test_rv_lists_bit_exact(bcd, which, request):
         assert np.array_equal(bcd.bc_rv_compute(dg, int(r)), O.rv(og, int(r))), r
 
 
-@pytest.mark.parametrize("tile_words", [1, 2, 4])
+@pytest.mark.parametrize("tile_words", [1, 2, 4, 8])
 def test_probe_dist_sigma_delta(bcd, er1, tile_words):
     g, og = er1
     dg = make(bcd, g, tile_words=tile_words)
@@ -83,7 +83,7 @@ def test_probe_dist_sigma_delta(bcd, er1, tile_words):
 
 
 @pytest.mark.parametrize("cfg", [{}, {"tile_words": 1}, {"tile_words": 2}, {"tile_words": 4, "blocks_per_sm": 1},
-                                 {"tile_words": 4, "blocks_per_sm": 2}, {"chunk_arcs": 32},
+                                 {"tile_words": 4, "blocks_per_sm": 2}, {"tile_words": 8}, {"chunk_arcs": 32},
                                  {"block_threads": 256, "chunk_arcs": 64}])
 def test_exact_matches_oracle(bcd, er1, cfg):
     g, og = er1

@@ -336,7 +336,7 @@ def test_scan_repeated_launches(bcd, er1):
 # ------------------------------------------------ several query vertices (accumulation = 3)
 
 @pytest.mark.parametrize("cfg", [{}, {"tile_words": 1}, {"tile_words": 2, "chunk_arcs": 32},
-                                 {"tile_words": 4, "blocks_per_sm": 1}])
+                                 {"tile_words": 4, "blocks_per_sm": 1}, {"tile_words": 8}])
 def test_multi_vertex_scan_exact(bcd, er1, cfg):
     """A batch of exact queries at 20 distinct vertices (three passes of 8
     columns) with repeated vertices, against the oracle's E-BCD."""
