@@ -318,12 +318,22 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                 p.lev_start[seg] = es;
                 p.lev_dist[seg] = d;
             }
-            // step 1: the slot's pairs, one per lane; short rows finish here
+            // step 1: the slot's pairs; short rows finish here. A pair gets
+            // LPP lanes (1, 2, 4 or 8: the most with which the level's pairs
+            // still fit the grid's lanes once), each walking every LPP-th arc
+            // of its rows, so a level with few pairs does not wait on one lane
+            // walking a whole row; the subgroup's sigma parts meet in a fixed
+            // shuffle tree (integers: exact).
             {
-                ChunkGrabber grab(&wl[kGrabPairs * LS + seg], (cnt + 31) / 32, nwarps);
+                int LPP = 1;
+                while (LPP < 8 && cnt * (long long)(2 * LPP) <= 32 * nwarps) LPP <<= 1;
+                const int per = 32 / LPP;  // pairs per warp step
+                const int sub = lane / LPP, rl = lane % LPP;
+                const bool lead = rl == 0;
+                ChunkGrabber grab(&wl[kGrabPairs * LS + seg], (cnt + per - 1) / per, nwarps);
                 long long gi;
                 while (grab.next(gi, lane)) {
-                    const long long i = gi * 32 + lane;
+                    const long long i = gi * per + sub;
                     int x = 0, s = 0;
                     bool ok = false;
                     if (i < cnt) {
@@ -332,44 +342,59 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                         s = (int)(pk & (uint32_t)(S - 1));
                         ok = p.dist[((size_t)x << tl.shift) + s] == du;
                     }
-                    const unsigned am = __ballot_sync(kFull, ok);
+                    const unsigned am = __ballot_sync(kFull, ok && lead);
                     if (am == 0u) continue;
                     unsigned long long eb = 0;
                     if (lane == 0) eb = atomicAdd(&p.lev_cnt[seg], (unsigned long long)__popc(am));
                     eb = __shfl_sync(kFull, eb, 0);
-                    if (!ok) continue;
-                    const long long e = es + (long long)eb + __popc(am & ((1u << lane) - 1u));
-                    if (e >= p.hcap) {
-                        set_err(p.ctr, kDevHistOverflow);
-                        continue;
+                    const long long e = es + (long long)eb + __popc(am & ((1u << (sub * LPP)) - 1u));
+                    bool go = ok;
+                    if (go && e >= p.hcap) {
+                        if (lead) set_err(p.ctr, kDevHistOverflow);
+                        go = false;
                     }
-                    p.hv[e] = x;
-                    p.hs[e] = (uint16_t)s;
-                    const long long rb = __ldg(p.off + x), re = __ldg(p.off + x + 1);
-                    const long long irb = __ldg(p.roff + x), ire = d > 0 ? __ldg(p.roff + x + 1) : irb;
-                    st.reached += 1;
-                    st.edges += (unsigned)(re - rb);
-                    if (atomicCAS(&p.tag[x], -1, 0) == -1) {
-                        st.vb += 1;
-                        st.eb += (unsigned)(re - rb);
+                    long long rb = 0, re = 0, irb = 0, ire = 0;
+                    if (go) {
+                        rb = __ldg(p.off + x);
+                        re = __ldg(p.off + x + 1);
+                        irb = __ldg(p.roff + x);
+                        ire = d > 0 ? __ldg(p.roff + x + 1) : irb;
                     }
-                    const uint64_t qm = __ldg(p.qmask + x);
-                    if (qm) {
-                        uint64_t y = qm & s_need[s];
-                        while (y) {
-                            const int q = __ffsll((long long)y) - 1;
-                            y &= y - 1;
-                            p.qlevel[s * 64 + q] = seg;
+                    if (go && lead) {
+                        p.hv[e] = x;
+                        p.hs[e] = (uint16_t)s;
+                        st.reached += 1;
+                        st.edges += (unsigned)(re - rb);
+                        if (atomicCAS(&p.tag[x], -1, 0) == -1) {
+                            st.vb += 1;
+                            st.eb += (unsigned)(re - rb);
+                        }
+                        const uint64_t qm = __ldg(p.qmask + x);
+                        if (qm) {
+                            uint64_t y = qm & s_need[s];
+                            while (y) {
+                                const int q = __ffsll((long long)y) - 1;
+                                y &= y - 1;
+                                p.qlevel[s * 64 + q] = seg;
+                            }
                         }
                     }
+                    const bool shortrow = go && re - rb <= p.wshort && ire - irb <= p.wshort;
+                    double part = 0.0;
+                    if (shortrow && d > 0) part = pull_sigma(p, tl, s, du, irb + rl, ire, LPP, st.tight);
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1)
+                        if (o < LPP) part += __shfl_xor_sync(kFull, part, o);
                     double *sp = p.sigma + ((size_t)x << tl.shift) + s;
-                    if (re - rb <= p.wshort && ire - irb <= p.wshort) {
-                        const double sg = d > 0 ? pull_sigma(p, tl, s, du, irb, ire, 1, st.tight) : 1.0;
-                        *sp = sg;
-                        if (sg >= kTwo53) flag_source(p, s);
-                        relax_row(p, tl, s, du, rb, re, 1);
-                        st.arcs += (unsigned)((re - rb) + (ire - irb));
-                    } else {
+                    if (shortrow) {
+                        if (lead) {
+                            const double sg = d > 0 ? part : 1.0;
+                            *sp = sg;
+                            if (sg >= kTwo53) flag_source(p, s);
+                            st.arcs += (unsigned)((re - rb) + (ire - irb));
+                        }
+                        relax_row(p, tl, s, du, rb + rl, re, LPP);
+                    } else if (go && lead) {
                         if (d == 0) *sp = 1.0;
                         const int nin = (int)((ire - irb + CH - 1) / CH);
                         const int nout = (int)((re - rb + CH - 1) / CH);
