@@ -391,9 +391,24 @@ void bc_server_destroy(bc_server *srv);
  *                  (1..1024, default 32).
  *   timeout_us     limit, in microseconds of wall time, on every wait of a
  *                  traversal kernel at a grid-wide barrier (default
- *                  10,000,000: 10 s). A wait that runs out makes every block
- *                  leave the kernel; the call returns BC_E_TIMEOUT, the
- *                  graph's device state is reset and the handle stays usable.
+ *                  10,000,000: 10 s), and on the time one block of the
+ *                  weighted source kernel spends on one source. A wait or a
+ *                  source that runs out makes every block leave the kernel;
+ *                  the call returns BC_E_TIMEOUT, the graph's device state
+ *                  is reset and the handle stays usable.
+ *   weighted_kernel  organisation of the weighted SPD: 1 the tile kernel
+ *                  (the 64 * weighted_words sources of a tile settle their
+ *                  (vertex, source) pairs together, one grid-wide barrier
+ *                  per distance value); 2 (default) the source kernel: each
+ *                  block takes one source at a time and settles its
+ *                  distances with block barriers only, so blocks never wait
+ *                  on one another (per block: 20 bytes per vertex plus the
+ *                  bucket ring; as many blocks as fit in half of the free
+ *                  device memory, up to the resident maximum). Both give
+ *                  the same distances and sigma; dependencies agree up to
+ *                  fp64 summation order. The traversal rooted at the query
+ *                  vertices of the vertex scan, and bc_spd_probe, always
+ *                  run on the tile kernel.
  * Zero fields keep their current value.
  */
 typedef struct {
@@ -407,6 +422,7 @@ typedef struct {
     int32_t timeout_us;
     int32_t pull_permille;
     int32_t weighted_short_row;
+    int32_t weighted_kernel;
 } bc_config;
 
 bc_status bc_set_config(bc_graph *g, const bc_config *cfg);

@@ -80,7 +80,7 @@ class bc_config(C.Structure):
     _fields_ = [("tile_words", C.c_int32), ("chunk_arcs", C.c_int32), ("block_threads", C.c_int32),
                 ("source_order", C.c_int32), ("blocks_per_sm", C.c_int32), ("weighted_words", C.c_int32),
                 ("accumulation", C.c_int32), ("timeout_us", C.c_int32), ("pull_permille", C.c_int32),
-                ("weighted_short_row", C.c_int32)]
+                ("weighted_short_row", C.c_int32), ("weighted_kernel", C.c_int32)]
 
 
 class bc_tune_report(C.Structure):
@@ -238,10 +238,11 @@ def bc_set_stream(g: Graph, stream):
 
 
 def bc_set_config(g: Graph, tile_words=0, chunk_arcs=0, block_threads=0, source_order=0, blocks_per_sm=0,
-                  weighted_words=0, accumulation=0, timeout_us=0, pull_permille=0, weighted_short_row=0):
+                  weighted_words=0, accumulation=0, timeout_us=0, pull_permille=0, weighted_short_row=0,
+                  weighted_kernel=0):
     c = bc_config(int(tile_words), int(chunk_arcs), int(block_threads), int(source_order), int(blocks_per_sm),
                   int(weighted_words), int(accumulation), int(timeout_us), int(pull_permille),
-                  int(weighted_short_row))
+                  int(weighted_short_row), int(weighted_kernel))
     _check(lib().bc_set_config(g.handle, C.byref(c)))
 
 

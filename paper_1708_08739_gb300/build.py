@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbcd.so")
-SOURCES = ["bcd_graph.cu", "bcd_scan.cu", "bcd_traverse.cu", "bcd_wtraverse.cu", "bcd_query.cu", "bcd_server.cu", "bcd_noalloc.cu"]
+SOURCES = ["bcd_graph.cu", "bcd_scan.cu", "bcd_traverse.cu", "bcd_wtraverse.cu", "bcd_wsrc.cu", "bcd_query.cu", "bcd_server.cu", "bcd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

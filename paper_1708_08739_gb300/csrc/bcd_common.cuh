@@ -232,6 +232,24 @@ struct bcd_workspace {
     int32_t *rtile = nullptr;     // [64 * W] the one-source tile of the query vertex's traversal
     uint32_t *qflags = nullptr;   // [64]
     uint64_t *srcflag = nullptr;  // [W]
+    // weighted source kernel (one source per block): per-block state
+    int32_t sblocks = 0;                   // blocks the state is sized for
+    unsigned long long *sdist = nullptr;   // [sblocks * n]
+    double *ssig = nullptr;                // [sblocks * n]
+    int32_t *shv = nullptr;                // [sblocks * n]
+    int32_t *slstart = nullptr;            // [sblocks * smaxlev]
+    unsigned long long *sldist = nullptr;  // [sblocks * smaxlev]
+    uint32_t *sbk = nullptr;               // [sblocks * ring * sbcap]
+    bcd::Chunk *sch = nullptr;             // [sblocks * schcap]
+    double *spart = nullptr;               // [sblocks * schcap]
+    int64_t sbcap = 0;
+    int64_t schcap = 0;
+    int32_t smaxlev = 0;
+    double *sdep = nullptr;                // [sources * 64] per-source dependencies
+    int64_t sdep_cap = 0;
+    uint32_t *sflag = nullptr;             // [sources]
+    int64_t sflag_cap = 0;
+    unsigned long long *snext = nullptr;   // source hand-out counter
     bcd::Counters *ctr = nullptr;
     int64_t *scratch64 = nullptr; // [scratch_len + 256] scan/compaction scratch, counts past scratch_len
     int64_t scratch_len = 0;
@@ -287,6 +305,7 @@ struct bc_graph {
     int accumulation = 4;         // 1: Eq. 4 push, 2: vertex scan for one-vertex groups, 3: scan always, 4: chosen per group
     int pull_permille = 0;        // bottom-up levels: frontier out-arcs >= pull_permille / 1000 of m (0: never)
     int wshort = 32;              // weighted kernel: longest row one lane walks alone
+    int weighted_kernel = 2;      // weighted graphs: 1 tile kernel, 2 one source per block
     bcd_workspace ws;
     int64_t launches = 0;
     int last_grid = 0;                       // blocks of the last traversal launch
@@ -333,6 +352,11 @@ void free_workspace(bc_graph *g);
 // traversal launcher (bcd_traverse.cu)
 bc_status run_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out);
 bc_status launch_weighted(bc_graph *g, TravParams &p);  // bcd_wtraverse.cu
+// weighted source kernel (bcd_wsrc.cu): whether a launch goes to it, the
+// launcher (same contract as run_traversal) and its state's release
+bool src_kernel_applies(const bc_graph *g, const TravParams &p);
+bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, unsigned long long *edges_out);
+void free_src_state(bc_graph *g);
 
 // query preparation and slices for the serving loop (bcd_query.cu)
 struct PrepItem {

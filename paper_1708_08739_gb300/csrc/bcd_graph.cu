@@ -175,6 +175,9 @@ bc_status bc_set_config(bc_graph *g, const bc_config *c) {
     if (c->weighted_short_row && (c->weighted_short_row < 1 || c->weighted_short_row > 1024))
         return set_error(BC_E_INVALID_ARG, "bc_set_config: weighted_short_row must be 1..1024 (0 keeps it)");
     if (c->weighted_short_row) g->wshort = c->weighted_short_row;
+    if (c->weighted_kernel && c->weighted_kernel != 1 && c->weighted_kernel != 2)
+        return set_error(BC_E_INVALID_ARG, "bc_set_config: weighted_kernel must be 1 or 2 (0 keeps it)");
+    if (c->weighted_kernel) g->weighted_kernel = c->weighted_kernel;
     if (c->timeout_us) g->timeout_ns = 1000.0 * (double)c->timeout_us;
     if (c->accumulation) g->accumulation = c->accumulation;
     if (c->tile_words) g->tile_words = c->tile_words;
@@ -195,6 +198,7 @@ bc_status bc_get_config(const bc_graph *g, bc_config *c) {
     c->timeout_us = (int32_t)(g->timeout_ns / 1000.0);
     c->pull_permille = g->pull_permille > 0 ? g->pull_permille : -1;
     c->weighted_short_row = g->wshort;
+    c->weighted_kernel = g->weighted_kernel;
     return BC_OK;
 }
 

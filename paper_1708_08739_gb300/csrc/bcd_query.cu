@@ -370,6 +370,7 @@ void free_workspace(bc_graph *g) {
     dev_free(ws.scratch64);
     dev_free(ws.small);
     dev_free(ws.tile_partial);
+    free_src_state(g);
     dev_free(ws.mult);
     dev_free(ws.rvlists);
     dev_free(ws.draws);
@@ -1000,7 +1001,7 @@ static bc_status run_group(bc_graph *g, std::vector<GQuery> &qs, bc_result *res,
             p.srcflag = ws.srcflag;
             int lv = 0;
             unsigned long long ed = 0;
-            BCD_TRY(run_traversal(g, W, p, &lv, &ed));
+            BCD_TRY(src_kernel_applies(g, p) ? run_src_traversal(g, W, p, &lv, &ed) : run_traversal(g, W, p, &lv, &ed));
             levels = std::max(levels, lv);
             edges += ed;
             tm.fwd += g->last_ns_fwd * 1e-6;
@@ -1262,7 +1263,8 @@ bc_status run_slice(bc_graph *g, const std::vector<int32_t> &srcs, const std::ve
         p.srcflag = ws.srcflag;
         g->launches += 1;
         unsigned long long ed = 0;
-        BCD_TRY(run_traversal(g, W, p, nullptr, &ed));
+        BCD_TRY(src_kernel_applies(g, p) ? run_src_traversal(g, W, p, nullptr, &ed)
+                                          : run_traversal(g, W, p, nullptr, &ed));
         if (edges) *edges += ed;
         return BC_OK;
     };

@@ -58,13 +58,16 @@ def test_barrier_timeout_then_recovery(bcd, er):
     assert close(bcd.bc_approx_T(dg, qs[1], 300, 7)[0], w)
 
 
-def test_weighted_barrier_timeout_then_recovery(bcd):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_weighted_barrier_timeout_then_recovery(bcd, kernel):
+    """Tile kernel: a grid-barrier wait runs out; source kernel: a block's
+    source runs past the limit (checked after each distance level)."""
     g = gg.erdos_renyi(600, 4000, 21)
     g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     og = O.Graph.from_csr(g)
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
     qs = gg.random_vertices(g.n, 4, 104).tolist()
-    bcd.bc_set_config(dg, timeout_us=1)
+    bcd.bc_set_config(dg, timeout_us=1, weighted_kernel=kernel)
     with pytest.raises(bcd.BCError) as e:
         bcd.bc_batch(dg, [{"r": r} for r in qs])
     assert e.value.status == bcd.BC_E_TIMEOUT

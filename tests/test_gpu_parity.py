@@ -292,7 +292,10 @@ def wer():
     return [(x, O.Graph.from_csr(x)) for x in (g255, g3)]
 
 
-WCFGS = [{}, {"weighted_words": 1}, {"weighted_words": 4, "chunk_arcs": 32}]
+WCFGS = [{}, {"weighted_words": 1}, {"weighted_words": 4, "chunk_arcs": 32},
+         {"weighted_kernel": 1}, {"weighted_kernel": 1, "weighted_words": 1},
+         {"weighted_kernel": 1, "weighted_words": 4, "chunk_arcs": 32},
+         {"weighted_short_row": 2, "chunk_arcs": 32, "block_threads": 128}]
 
 
 @pytest.mark.parametrize("cfg", WCFGS)
@@ -358,7 +361,8 @@ def test_weighted_closed_forms_and_sampling(bcd, wer):
         assert info["rv_size"] == k and close(got, want)
 
 
-@pytest.mark.parametrize("cfg", [{}, {"weighted_words": 2, "chunk_arcs": 64}])
+@pytest.mark.parametrize("cfg", [{}, {"weighted_words": 2, "chunk_arcs": 64}, {"weighted_kernel": 1},
+                                 {"weighted_short_row": 8, "block_threads": 256}])
 def test_weighted_rmat_small(bcd, cfg):
     """A small weighted R-MAT (the weighted configuration at scale 12): hub
     rows of hundreds of arcs go through the chunked path."""
@@ -371,6 +375,43 @@ def test_weighted_rmat_small(bcd, cfg):
     for r, o in zip(qs, out):
         want = O.bc_exact(og, r, 0)[0]
         assert close(o["bc"], want), (r, o["bc"], want)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_weighted_growth_paths_closed_forms(bcd, kernel):
+    """Capacities that start too small and grow on the rerun.
+    - A directed path of 10,000 vertices with weights 1..2 has about 15,000
+      distinct distances from its first vertex (more than the initial level
+      arrays hold); BC(r) = r (n - 1 - r) whatever the weights.
+    - An out-star of 20,000 leaves of weight 1, each leaf with an arc to one
+      sink, queues every leaf at distance 1 from the centre (more than a
+      ring slot of the source kernel holds at first) and gives the sink
+      20,000 in-arcs: BC(leaf) = 1 / 20,000, BC(centre) = BC(sink) = 0.
+    - The same star with arcs to two sinks, and every row longer than one
+      arc cut into chunks: two chunks per leaf at distance 1 (more than the
+      source kernel's chunk list holds at first); BC(leaf) = 2 / 20,000."""
+    n = 10000
+    w = gg.uniform_weights(n - 1, 1, 2, 9)
+    path = csr(n, [(i, i + 1) for i in range(n - 1)], w.tolist())
+    dg = make(bcd, path, weighted_kernel=kernel)
+    rs = [1, 300, 2000]
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in rs])
+    for r, o in zip(rs, out):
+        assert o["status"] == 0 and o["bc"] == float(r * (n - 1 - r)), (r, o)
+    dg.close()
+    L = 20000
+    arcs = [(0, 1 + i) for i in range(L)] + [(1 + i, L + 1) for i in range(L)]
+    star = csr(L + 2, arcs, [1] * len(arcs))
+    dg = make(bcd, star, weighted_kernel=kernel)
+    out, _ = bcd.bc_batch(dg, [{"r": 1}, {"r": 777}, {"r": 0}, {"r": L + 1}])
+    assert [o["bc"] for o in out] == [1.0 / L, 1.0 / L, 0.0, 0.0], out
+    dg.close()
+    arcs2 = [(0, 1 + i) for i in range(L)] + [(1 + i, L + 1) for i in range(L)] + [(1 + i, L + 2) for i in range(L)]
+    star2 = csr(L + 3, arcs2, [1] * len(arcs2))
+    dg = make(bcd, star2, weighted_kernel=kernel, weighted_short_row=1, chunk_arcs=32)
+    out, _ = bcd.bc_batch(dg, [{"r": 1}, {"r": L}, {"r": L + 2}])
+    assert [o["bc"] for o in out] == [2.0 / L, 2.0 / L, 0.0], out
+    dg.close()
 
 
 def test_device_input_arrays(bcd, er1):

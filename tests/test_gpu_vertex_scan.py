@@ -79,6 +79,12 @@ def test_config_roundtrip(bcd, er1):
         bcd.bc_set_config(dg, tile_words=4, block_threads=192)
     assert e.value.status == bcd.BC_E_INVALID_ARG
     assert bcd.bc_get_config(dg)["tile_words"] == 2
+    assert bcd.bc_get_config(dg)["weighted_kernel"] == 2
+    bcd.bc_set_config(dg, weighted_kernel=1)
+    assert bcd.bc_get_config(dg)["weighted_kernel"] == 1
+    with pytest.raises(bcd.BCError) as e:
+        bcd.bc_set_config(dg, weighted_kernel=3)
+    assert e.value.status == bcd.BC_E_INVALID_ARG
 
 
 @pytest.mark.parametrize("cfg", [{"tile_words": 1}, {"tile_words": 2}, {"tile_words": 4, "blocks_per_sm": 1},
