@@ -234,8 +234,7 @@ struct bcd_workspace {
     uint64_t *srcflag = nullptr;  // [W]
     // weighted source kernel (one source per block): per-block state
     int32_t sblocks = 0;                   // blocks the state is sized for
-    unsigned long long *sdist = nullptr;   // [sblocks * n]
-    double *ssig = nullptr;                // [sblocks * n]
+    unsigned long long *sds = nullptr;     // [sblocks * n * 2]: (distance, sigma) of each vertex
     int32_t *shv = nullptr;                // [sblocks * n]
     int32_t *slstart = nullptr;            // [sblocks * smaxlev]
     unsigned long long *sldist = nullptr;  // [sblocks * smaxlev]

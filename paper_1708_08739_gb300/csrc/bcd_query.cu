@@ -1587,6 +1587,7 @@ bc_status bc_tune(bc_graph *g, const bc_query *queries, int64_t nq, int64_t prob
     // the search space, one parameter at a time (0 ends a list)
     std::vector<std::pair<int32_t bc_config::*, std::vector<int32_t>>> space;
     if (g->weighted) {
+        space.push_back({&bc_config::weighted_kernel, {1, 2}});
         space.push_back({&bc_config::weighted_words, {2, 4, 8}});
         space.push_back({&bc_config::weighted_short_row, {16, 32, 64}});
         space.push_back({&bc_config::chunk_arcs, {64, 128, 256}});

@@ -8,28 +8,37 @@
 // them per tile with weights up to 255) is gone, and so is the idle time of
 // every lane waiting there for the slowest chain of the level.
 //
-// State of a block, for its current source s: dist[v] (uint64, all ones when
-// unreached), sigma[v] (then c = (1 + delta) / sigma in place during the
-// Eq. 4 pass), the settled vertices in settling order (history) with the
-// start and distance of each distance level, and the bucket ring: R slots (R
-// a power of two above the largest weight) of bcap queued vertices each, with
-// their queued / consumed counters in shared memory. A relaxation that lowers
-// dist[y] (atomicMin) queues y in the slot of the new distance; when slot d
-// comes up, a queued vertex still at distance d is settled (each vertex once:
-// a vertex is queued only when its distance strictly drops), stale entries
-// are skipped. Every tight in-arc predecessor of a vertex settled at d sits
-// at a smaller distance, so sigma is complete when it is pulled.
+// State of a block, for its current source s: one 16-byte pair per vertex v,
+// (dist(v), sigma(v)) (distance all ones when unreached; during the Eq. 4
+// pass c(v) = (1 + delta(v)) / sigma(v) replaces sigma in place), the settled
+// vertices in settling order (history) with the start and distance of each
+// distance level, and the bucket ring: R slots (R a power of two above the
+// largest weight) of bcap queued vertices each, with their queued / consumed
+// counters in shared memory.
+//
+// Sigma rides along the relaxations. Settling u at distance d (its sigma is
+// final: every predecessor on a shortest path sits at a smaller distance and
+// relaxed its arcs in an earlier level), each out-arc (u, v, w) offers the
+// candidate nd = d + w: if nd is below dist(v) the pair becomes (nd,
+// sigma(u)) and v is queued in the slot of nd; if nd equals dist(v),
+// sigma(u) is added. The pair changes by one 16-byte compare-and-swap, so a
+// distance and its path count always move together, and when v settles its
+// pair holds its distance with the sum over exactly its tight in-arcs (sigma
+// values are integers: exact in any order below 2^53). Every arc is read
+// once in the forward pass, along its tail's out-row; no in-arc pass.
+// A vertex queued in the slot of d whose distance has since dropped is stale
+// and skipped; a vertex is queued only when its distance strictly drops, so
+// it settles once.
 //
 // A level's queued vertices are spread over the block's lanes, 1 to 32 lanes
 // per vertex (as many as the level's size leaves room for); each lane walks
-// every LPP-th arc and the parts of sigma meet in a fixed shuffle tree.
-// Vertices with a row of more than weighted_short_row arcs are cut into
-// chunk_arcs chunks that warps take after a block barrier (lanes over arcs);
-// the in-arc chunks' sigma parts are added in chunk order. Sigma values are
-// integers, so they are exact in any order below 2^53, and the source is
-// flagged when one reaches 2^53. The Eq. 4 pass walks the levels from the
-// deepest to the shallowest level holding a query vertex the source serves,
-// with the same split: delta is the same from run to run.
+// every LPP-th arc. Vertices with more than weighted_short_row out-arcs are
+// cut into chunk_arcs chunks that warps take after a block barrier (lanes
+// over arcs). The source is flagged when a sigma reaches 2^53. The Eq. 4
+// pass walks the levels from the deepest to the shallowest level holding a
+// query vertex the source serves, summing c over tight out-arcs (short rows
+// by LPP lanes and a fixed shuffle tree, long rows by chunks added in chunk
+// order), so delta is the same from run to run.
 //
 // Each source's dependencies delta_s.(r_q) go to sdep[i * 64 + q] (i its
 // position in the launch's source list, q the queries that need it); a
@@ -52,15 +61,20 @@ using namespace dev;
 constexpr int kLanesBatch = 4;  // arcs a lane loads together
 constexpr double kSrcTwo53 = 9007199254740992.0;
 
+// (distance, sigma) of one vertex for the block's current source
+struct __align__(16) DistSig {
+    unsigned long long d;
+    double s;
+};
+
 struct SrcParams {
-    unsigned long long *dist;   // [blocks * n]
-    double *sig;                // [blocks * n]
+    DistSig *ds;                // [blocks * n]
     int32_t *hv;                // [blocks * n] settled vertices of the current source
     int32_t *lstart;            // [blocks * maxlev] first history entry of each level
     unsigned long long *ldist;  // [blocks * maxlev] distance of each level
     uint32_t *bk;               // [blocks * ring * bcap] queued vertices, circular per slot
     Chunk *ch;                  // [blocks * chcap] long-row chunks of one level
-    double *part;               // [blocks * chcap] in-arc chunk sums
+    double *part;               // [blocks * chcap] backward chunk sums
     double *sdep;               // [nsrc * 64]
     uint32_t *sflag;            // [nsrc] sigma >= 2^53 seen
     unsigned long long *next;   // source hand-out
@@ -82,13 +96,41 @@ __device__ __forceinline__ double sum_warp(double x) {
     return x;
 }
 
-// Relaxes out-arcs a, a + step, ... < ae of a vertex settled at distance d.
-__device__ __forceinline__ void src_relax(const TravParams &p, unsigned long long *dist, uint32_t *bk,
-                                          uint32_t *s_cnt, int64_t bcap, int R, unsigned long long d, long long a,
-                                          long long ae, int step) {
+// 16-byte compare-and-swap of a (distance, sigma) pair: true when *p held
+// `expect` and now holds `nw`; otherwise `expect` receives what *p held.
+__device__ __forceinline__ bool cas_pair(DistSig *p, DistSig &expect, const DistSig &nw) {
+    const unsigned long long e0 = expect.d, e1 = (unsigned long long)__double_as_longlong(expect.s);
+    const unsigned long long n0 = nw.d, n1 = (unsigned long long)__double_as_longlong(nw.s);
+    unsigned long long o0, o1;
+    asm volatile(
+        "{\n\t.reg .b128 e, n, o;\n\t"
+        "mov.b128 e, {%2, %3};\n\t"
+        "mov.b128 n, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], e, n;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(o0), "=l"(o1)
+        : "l"(e0), "l"(e1), "l"(n0), "l"(n1), "l"(p)
+        : "memory");
+    const bool ok = o0 == e0 && o1 == e1;
+    expect.d = o0;
+    expect.s = __longlong_as_double((long long)o1);
+    return ok;
+}
+
+constexpr int kCasTries = 1 << 16;  // a pair changed under us this often: give up (never seen)
+
+// Offers out-arcs a, a + step, ... < ae of a vertex settled at distance d
+// with path count sg: lowers a head's distance (and queues it) or adds sg to
+// its count when the candidate ties. Returns false if a pair kept changing
+// past kCasTries attempts.
+__device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint32_t *bk, uint32_t *s_cnt,
+                                          int64_t bcap, int R, unsigned long long d, double sg, long long a,
+                                          long long ae, int step, unsigned long long &adds) {
+    bool fine = true;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
-        unsigned long long nd[kLanesBatch], cur[kLanesBatch];
+        unsigned long long nd[kLanesBatch];
+        DistSig cur[kLanesBatch];
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
             const long long aj = a + (long long)j * step;
@@ -96,58 +138,47 @@ __device__ __forceinline__ void src_relax(const TravParams &p, unsigned long lon
             nd[j] = aj < ae ? d + __ldg(p.wt + aj) : 0ull;
         }
 #pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) cur[j] = y[j] >= 0 ? dist[y[j]] : 0ull;
+        for (int j = 0; j < kLanesBatch; ++j) {
+            if (y[j] >= 0) {
+                cur[j] = ds[y[j]];
+            } else {
+                cur[j].d = 0ull;
+                cur[j].s = 0.0;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
-            if (y[j] >= 0 && nd[j] < cur[j]) {
-                const unsigned long long old = atomicMin(dist + y[j], nd[j]);
-                if (nd[j] < old) {
-                    const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
-                    const uint32_t pos = atomicAdd(&s_cnt[slot], 1u);
-                    bk[(size_t)slot * (size_t)bcap + (pos & (uint32_t)(bcap - 1))] = (uint32_t)y[j];
+            if (y[j] < 0 || nd[j] > cur[j].d) continue;
+            DistSig *q = ds + y[j];
+            for (int it = 0;; ++it) {
+                if (nd[j] > cur[j].d) break;
+                const bool lower = nd[j] < cur[j].d;
+                DistSig nw;
+                nw.d = nd[j];
+                nw.s = lower ? sg : cur[j].s + sg;
+                if (cas_pair(q, cur[j], nw)) {
+                    adds += 1;
+                    if (lower) {
+                        const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
+                        const uint32_t pos = atomicAdd(&s_cnt[slot], 1u);
+                        bk[(size_t)slot * (size_t)bcap + (pos & (uint32_t)(bcap - 1))] = (uint32_t)y[j];
+                    }
+                    break;
+                }
+                if (it >= kCasTries) {
+                    fine = false;
+                    break;
                 }
             }
         }
     }
-}
-
-// Sum of sigma(u) over the tight in-arcs (u at distance d - w(u, v)) among
-// a, a + step, ... < ae of a vertex at distance d.
-__device__ __forceinline__ double src_pull_sigma(const TravParams &p, const unsigned long long *dist,
-                                                 const double *sig, unsigned long long d, long long a, long long ae,
-                                                 int step, unsigned long long &tight) {
-    double acc = 0.0;
-    for (; a < ae; a += kLanesBatch * step) {
-        int u[kLanesBatch];
-        unsigned long long want[kLanesBatch];
-        bool ok[kLanesBatch];
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) {
-            const long long aj = a + (long long)j * step;
-            const unsigned long long w = aj < ae ? (unsigned long long)__ldg(p.rwt + aj) : ~0ull;
-            ok[j] = w <= d;
-            u[j] = ok[j] ? __ldg(p.rcol + aj) : 0;
-            want[j] = d - w;
-        }
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) ok[j] = ok[j] && dist[u[j]] == want[j];
-        double v[kLanesBatch];
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) v[j] = ok[j] ? sig[u[j]] : 0.0;
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j)
-            if (ok[j]) {
-                acc += v[j];
-                tight += 1;
-            }
-    }
-    return acc;
+    return fine;
 }
 
 // Sum of c(y) over the tight out-arcs (y at distance d + w(v, y)) among a,
 // a + step, ... < ae of a vertex at distance d.
-__device__ __forceinline__ double src_pull_c(const TravParams &p, const unsigned long long *dist, const double *sig,
-                                             unsigned long long d, long long a, long long ae, int step) {
+__device__ __forceinline__ double src_pull_c(const TravParams &p, const DistSig *ds, unsigned long long d, long long a,
+                                             long long ae, int step) {
     double acc = 0.0;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
@@ -160,14 +191,12 @@ __device__ __forceinline__ double src_pull_c(const TravParams &p, const unsigned
             y[j] = ok[j] ? __ldg(p.col + aj) : 0;
             want[j] = ok[j] ? d + __ldg(p.wt + aj) : 0ull;
         }
+        DistSig v[kLanesBatch];
 #pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) ok[j] = ok[j] && dist[y[j]] == want[j];
-        double v[kLanesBatch];
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) v[j] = ok[j] ? sig[y[j]] : 0.0;
+        for (int j = 0; j < kLanesBatch; ++j) v[j] = ds[y[j]];
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j)
-            if (ok[j]) acc += v[j];
+            if (ok[j] && v[j].d == want[j]) acc += v[j].s;
     }
     return acc;
 }
@@ -197,11 +226,11 @@ __device__ __forceinline__ void src_store_chunks(Chunk *chs, long long c0, int v
 }
 
 // delta(v) = sigma(v) * acc; c(v) = (1 + delta(v)) / sigma(v) replaces sigma(v).
-__device__ __forceinline__ void src_finalize(const TravParams &p, double *sig, uint64_t need, double *s_dep, int v,
+__device__ __forceinline__ void src_finalize(const TravParams &p, DistSig *ds, uint64_t need, double *s_dep, int v,
                                              double acc) {
-    const double sv = sig[v];
+    const double sv = ds[v].s;
     const double dd = sv * acc;
-    sig[v] = (1.0 + dd) / sv;
+    ds[v].s = (1.0 + dd) / sv;
     uint64_t y = __ldg(p.qmask + v) & need;
     while (y) {
         const int q = __ffsll((long long)y) - 1;
@@ -231,8 +260,7 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
     uint32_t *s_cnt = s_ring;
     uint32_t *s_base = s_ring + R;
     const size_t boff = (size_t)blockIdx.x * (size_t)q.n;
-    unsigned long long *dist = q.dist + boff;
-    double *sig = q.sig + boff;
+    DistSig *ds = q.ds + boff;
     int32_t *hv = q.hv + boff;
     int32_t *lstart = q.lstart + (size_t)blockIdx.x * (size_t)q.maxlev;
     unsigned long long *ldist = q.ldist + (size_t)blockIdx.x * (size_t)q.maxlev;
@@ -278,7 +306,8 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
         if (v0 < 0) continue;
         const uint64_t need = __ldg(p.need + v0);
         if (tid == 0) {
-            dist[v0] = 0ull;
+            ds[v0].d = 0ull;
+            ds[v0].s = 1.0;
             bk[0] = (uint32_t)v0;  // slot 0, position 0
             s_cnt[0] = 1u;
         }
@@ -325,28 +354,30 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                 for (long long gi = warp; gi < ngroups; gi += nwarps) {
                     const long long ii = gi * per + sub;
                     int x = 0;
-                    bool ok = false;
+                    DistSig px;
+                    px.d = ~0ull;
+                    px.s = 0.0;
                     if (ii < (long long)cnt) {
                         x = (int)bks[(b0 + (uint32_t)ii) & (uint32_t)(bcap - 1)];
-                        ok = dist[x] == d;
+                        px = ds[x];
                     }
+                    const bool ok = px.d == d;
                     const unsigned am = __ballot_sync(kFull, ok && lead);
                     if (am == 0u) continue;
                     int eb = 0;
                     if (lane == 0) eb = atomicAdd(&s_nh, __popc(am));
                     eb = __shfl_sync(kFull, eb, 0);
                     const int e = eb + __popc(am & ((1u << (sub * lpp)) - 1u));
-                    long long rb = 0, re = 0, irb = 0, ire = 0;
+                    long long rb = 0, re = 0;
                     if (ok) {
                         rb = __ldg(p.off + x);
                         re = __ldg(p.off + x + 1);
-                        irb = __ldg(p.roff + x);
-                        ire = d > 0 ? __ldg(p.roff + x + 1) : irb;
                     }
                     if (ok && lead) {
                         hv[e] = x;
                         st.reached += 1;
                         st.edges += (unsigned long long)(re - rb);
+                        if (px.s >= kSrcTwo53) s_flag = 1;
                         if (atomicCAS(&p.tag[x], -1, 0) == -1) {
                             st.vb += 1;
                             st.eb += (unsigned long long)(re - rb);
@@ -358,29 +389,20 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                             s_ql[qq] = seg;
                         }
                     }
-                    const bool shortrow = ok && re - rb <= p.wshort && ire - irb <= p.wshort;
-                    double sp = 0.0;
-                    if (shortrow && d > 0) sp = src_pull_sigma(p, dist, sig, d, irb + rl, ire, lpp, st.tight);
-                    sp = sum_lanes(sp, lpp);
-                    if (shortrow) {
-                        if (lead) {
-                            const double sg = d > 0 ? sp : 1.0;
-                            sig[x] = sg;
-                            if (sg >= kSrcTwo53) s_flag = 1;
-                            st.arcs += (unsigned long long)((re - rb) + (ire - irb));
+                    if (ok && re - rb <= p.wshort) {
+                        if (lead) st.arcs += (unsigned long long)(re - rb);
+                        if (!src_relax(p, ds, bk, s_cnt, bcap, R, d, px.s, rb + rl, re, lpp, st.tight)) {
+                            s_err = 1;
+                            set_err(p.ctr, kDevTimeout);
                         }
-                        src_relax(p, dist, bk, s_cnt, bcap, R, d, rb + rl, re, lpp);
                     } else if (ok && lead) {
-                        if (d == 0) sig[x] = 1.0;
-                        const int nin = (int)((ire - irb + CH - 1) / CH);
                         const int nout = (int)((re - rb + CH - 1) / CH);
-                        const int c0 = atomicAdd(nchp, nin + nout);
-                        if ((int64_t)c0 + nin + nout > q.chcap) {
+                        const int c0 = atomicAdd(nchp, nout);
+                        if ((int64_t)c0 + nout > q.chcap) {
                             s_err = 1;
                             set_err(p.ctr, kDevChunkOverflow);
                         } else {
-                            src_store_chunks(chs, c0, x, e, 1, irb, ire, nin, CH);
-                            src_store_chunks(chs, (long long)c0 + nin, x, e, 0, rb, re, nout, CH);
+                            src_store_chunks(chs, c0, x, e, 0, rb, re, nout, CH);
                         }
                     }
                 }
@@ -396,29 +418,19 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
             }
             const int nch = *nchp;
             if (s_err) return;
-            // step 2: long rows, lanes over arcs; then the in-arc sums in chunk order
+            // step 2: long out-rows, lanes over arcs
             if (nch > 0) {
                 for (int c = warp; c < nch; c += nwarps) {
                     const Chunk ch = load_chunk(&chs[c]);
-                    if (ch.pad & 1) {
-                        const double v = sum_warp(src_pull_sigma(p, dist, sig, d, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight));
-                        if (lane == 0) part[c] = v;
-                    } else {
-                        src_relax(p, dist, bk, s_cnt, bcap, R, d, ch.a0 + lane, ch.a0 + ch.na, 32);
+                    const double sg = ds[ch.v].s;
+                    if (!src_relax(p, ds, bk, s_cnt, bcap, R, d, sg, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight)) {
+                        s_err = 1;
+                        set_err(p.ctr, kDevTimeout);
                     }
                     if (lane < ch.na) st.arcs += (unsigned long long)((ch.na - lane + 31) / 32);
                 }
                 __syncthreads();
-                for (int c = tid; c < nch; c += bd) {
-                    const Chunk ch = load_chunk(&chs[c]);
-                    if ((ch.pad & 1) && ch.k == 0) {
-                        double acc = 0.0;
-                        for (int k = 0; k < ch.nch; ++k) acc += part[c + k];
-                        sig[ch.v] = acc;
-                        if (acc >= kSrcTwo53) s_flag = 1;
-                    }
-                }
-                __syncthreads();
+                if (s_err) return;
             }
             nh = s_nh;
             ++seg;
@@ -440,15 +452,16 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
             // delta_s.(r) = sigma_sr * sum over settled t with d(r, t) >= 1 and
             // d(s, r) + d(r, t) = d(s, t) of sigma_rt / sigma_st
             const int r = p.vroot;
-            const unsigned long long dsr = dist[r];
+            const DistSig pr = ds[r];
+            const unsigned long long dsr = pr.d;
             double acc = 0.0;
             if (dsr != ~0ull && need) {
                 for (int e = tid; e < nh; e += bd) {
                     const int t = hv[e];
                     const unsigned long long rd = p.rdist[t];
-                    const unsigned long long dt = dist[t];
-                    if (rd == 0ull || rd >= dt || dsr + rd != dt) continue;
-                    acc += p.rsig[t] / sig[t];
+                    const DistSig pt = ds[t];
+                    if (rd == 0ull || rd >= pt.d || dsr + rd != pt.d) continue;
+                    acc += p.rsig[t] / pt.s;
                     st.pairs += 1;
                 }
             }
@@ -458,7 +471,7 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
             if (tid == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < nwarps; ++w) sum += s_red[w];
-                const double dv = dsr != ~0ull ? sig[r] * sum : 0.0;
+                const double dv = dsr != ~0ull ? pr.s * sum : 0.0;
                 uint64_t y = need;
                 while (y) {
                     const int qq = __ffsll((long long)y) - 1;
@@ -478,12 +491,13 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                     cols |= 1ull << p.qcol[qq];
                 }
             }
-            for (int c = tid; c < 64; c += bd) s_cd[c] = ((cols >> c) & 1ull) ? dist[p.croot[c]] : ~0ull;
+            for (int c = tid; c < 64; c += bd) s_cd[c] = ((cols >> c) & 1ull) ? ds[p.croot[c]].d : ~0ull;
             __syncthreads();
             for (int e = tid; e < nh; e += bd) {
                 const int t = hv[e];
-                const unsigned long long dt = dist[t];
-                double sst = 0.0;
+                const DistSig pt = ds[t];
+                const unsigned long long dt = pt.d;
+                const double sst = pt.s;
                 uint64_t y = cols;
                 while (y) {
                     const int c = __ffsll((long long)y) - 1;
@@ -492,7 +506,6 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                     if (dc == ~0ull) continue;
                     const unsigned long long rd = p.rdistq[(size_t)t * 64 + c];
                     if (rd == 0ull || rd >= dt || dc + rd != dt) continue;
-                    if (sst == 0.0) sst = sig[t];
                     atomicAdd(&s_msum[c], p.rsigq[(size_t)t * 64 + c] / sst);
                     st.pairs += 1;
                 }
@@ -504,7 +517,7 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                     const int qq = __ffsll((long long)y) - 1;
                     y &= y - 1;
                     const int c = p.qcol[qq];
-                    s_dep[qq] = s_cd[c] != ~0ull ? sig[p.croot[c]] * s_msum[c] : 0.0;
+                    s_dep[qq] = s_cd[c] != ~0ull ? ds[p.croot[c]].s * s_msum[c] : 0.0;
                 }
             }
         } else {
@@ -540,10 +553,10 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                     }
                     const bool shortrow = ok && re - rb <= p.wshort;
                     double acc = 0.0;
-                    if (shortrow) acc = src_pull_c(p, dist, sig, dk, rb + rl, re, lpp);
+                    if (shortrow) acc = src_pull_c(p, ds, dk, rb + rl, re, lpp);
                     acc = sum_lanes(acc, lpp);
                     if (shortrow && lead) {
-                        src_finalize(p, sig, need, s_dep, v, acc);
+                        src_finalize(p, ds, need, s_dep, v, acc);
                         st.arcs += (unsigned long long)(re - rb);
                     } else if (ok && !shortrow && lead) {
                         const int nout = (int)((re - rb + CH - 1) / CH);
@@ -569,7 +582,7 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                 if (nch > 0) {
                     for (int c = warp; c < nch; c += nwarps) {
                         const Chunk ch = load_chunk(&chs[c]);
-                        const double v = sum_warp(src_pull_c(p, dist, sig, dk, ch.a0 + lane, ch.a0 + ch.na, 32));
+                        const double v = sum_warp(src_pull_c(p, ds, dk, ch.a0 + lane, ch.a0 + ch.na, 32));
                         if (lane == 0) part[c] = v;
                         if (lane < ch.na) st.arcs += (unsigned long long)((ch.na - lane + 31) / 32);
                     }
@@ -579,7 +592,7 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
                         if (ch.k == 0) {
                             double acc = 0.0;
                             for (int k = 0; k < ch.nch; ++k) acc += part[c + k];
-                            src_finalize(p, sig, need, s_dep, ch.v, acc);
+                            src_finalize(p, ds, need, s_dep, ch.v, acc);
                         }
                     }
                     __syncthreads();
@@ -591,9 +604,10 @@ __global__ void __launch_bounds__(512, 2) wsrc_kernel(TravParams p, SrcParams q)
         if (tid < 64 && ((need >> tid) & 1ull)) q.sdep[(size_t)si * 64 + tid] = s_dep[tid];
         if (tid == 0) q.sflag[si] = (uint32_t)s_flag;
         for (int e = tid; e < nh; e += bd) {
-            const int x = hv[e];
-            dist[x] = ~0ull;
-            sig[x] = 0.0;
+            DistSig z;
+            z.d = ~0ull;
+            z.s = 0.0;
+            ds[hv[e]] = z;
         }
         if (tid == 0) {
             const unsigned long long t = global_ns();
@@ -662,12 +676,28 @@ __global__ void wsrc_tile_sums(TravParams p, const double *sdep, const uint32_t 
 
 // Bytes of per-block state for a graph of n vertices.
 size_t src_block_bytes(int64_t n, int R, int64_t bcap, int64_t maxlev, int64_t chcap) {
-    return (size_t)n * (8 + 8 + 4) + (size_t)R * (size_t)bcap * 4 + (size_t)maxlev * 12 + (size_t)chcap * (32 + 8);
+    return (size_t)n * (16 + 4) + (size_t)R * (size_t)bcap * 4 + (size_t)maxlev * 12 + (size_t)chcap * (32 + 8);
+}
+
+// Every pair unreached: distance all ones, sigma zero.
+__global__ void clear_pairs(unsigned long long *ds, size_t npairs) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += (size_t)gridDim.x * blockDim.x) {
+        ds[2 * i] = ~0ull;
+        ds[2 * i + 1] = 0ull;  // +0.0
+    }
+}
+
+bc_status clear_src_pairs(bc_graph *g) {
+    bcd_workspace &ws = g->ws;
+    const size_t npairs = (size_t)ws.sblocks * (size_t)g->n;
+    clear_pairs<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(ws.sds, npairs);
+    g->launches += 1;
+    BCD_CUDA(cudaGetLastError());
+    return BC_OK;
 }
 
 void free_src_arrays(bcd_workspace &ws) {
-    dev_free(ws.sdist);
-    dev_free(ws.ssig);
+    dev_free(ws.sds);
     dev_free(ws.shv);
     dev_free(ws.slstart);
     dev_free(ws.sldist);
@@ -677,33 +707,28 @@ void free_src_arrays(bcd_workspace &ws) {
     ws.sblocks = 0;
 }
 
-// (Re)allocates the per-block state for the current capacities; the slabs
-// start cleared (all distances unreached, sigma zero).
+// (Re)allocates the per-block state for the current capacities; every pair
+// starts unreached.
 bc_status alloc_src_arrays(bc_graph *g, int blocks) {
     bcd_workspace &ws = g->ws;
     free_src_arrays(ws);
     const size_t B = (size_t)blocks;
     const size_t n = (size_t)g->n;
-    BCD_TRY(dev_alloc(&ws.sdist, B * n));
-    BCD_TRY(dev_alloc(&ws.ssig, B * n));
+    BCD_TRY(dev_alloc(&ws.sds, 2 * B * n));
     BCD_TRY(dev_alloc(&ws.shv, B * n));
     BCD_TRY(dev_alloc(&ws.slstart, B * (size_t)ws.smaxlev));
     BCD_TRY(dev_alloc(&ws.sldist, B * (size_t)ws.smaxlev));
     BCD_TRY(dev_alloc(&ws.sbk, B * (size_t)ws.ring * (size_t)ws.sbcap));
     BCD_TRY(dev_alloc(&ws.sch, B * (size_t)ws.schcap));
     BCD_TRY(dev_alloc(&ws.spart, B * (size_t)ws.schcap));
-    BCD_CUDA(cudaMemsetAsync(ws.sdist, 0xff, sizeof(unsigned long long) * B * n, g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.ssig, 0, sizeof(double) * B * n, g->stream));
     ws.sblocks = blocks;
-    return BC_OK;
+    return clear_src_pairs(g);
 }
 
 bc_status reset_src_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
-    if (!ws.sdist) return BC_OK;
-    const size_t cnt = (size_t)ws.sblocks * (size_t)g->n;
-    BCD_CUDA(cudaMemsetAsync(ws.sdist, 0xff, sizeof(unsigned long long) * cnt, g->stream));
-    BCD_CUDA(cudaMemsetAsync(ws.ssig, 0, sizeof(double) * cnt, g->stream));
+    if (!ws.sds) return BC_OK;
+    BCD_TRY(clear_src_pairs(g));
     if (ws.tag) BCD_CUDA(cudaMemsetAsync(ws.tag, 0xff, sizeof(int32_t) * (size_t)g->n, g->stream));
     return BC_OK;
 }
@@ -754,7 +779,7 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
     if (ws.sbcap == 0) {
         // queued vertices of one distance of one source: a few times the
         // average vertices per distance value; grown on overflow
-        int64_t b = 4096;
+        int64_t b = 8192;
         while (b < 4 * (int64_t)g->n / R && b < ((int64_t)1 << 30)) b *= 2;
         ws.sbcap = b;
         ws.schcap = 16384;
@@ -770,7 +795,7 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         blocks = (int)std::min<size_t>((size_t)blocks, budget / per);
         if (blocks < 1) return set_error(BC_E_OOM, "weighted source kernel: no room for one block's state");
     }
-    if (ws.sblocks != blocks || !ws.sdist) {
+    if (ws.sblocks != blocks || !ws.sds) {
         const bc_status st = alloc_src_arrays(g, blocks);
         if (st != BC_OK) {
             free_src_arrays(ws);
@@ -795,8 +820,7 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         p.timeout_ns = g->timeout_ns;
         p.cancel = g->cancel_d;
         SrcParams q;
-        q.dist = ws.sdist;
-        q.sig = ws.ssig;
+        q.ds = reinterpret_cast<DistSig *>(ws.sds);
         q.hv = ws.shv;
         q.lstart = ws.slstart;
         q.ldist = ws.sldist;

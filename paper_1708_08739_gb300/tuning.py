@@ -24,7 +24,7 @@ import numpy as np
 
 DEFAULT_TABLE = os.path.join(os.path.expanduser("~"), ".cache", "bcd", "tune.json")
 TUNED_FIELDS = ("tile_words", "blocks_per_sm", "chunk_arcs", "pull_permille", "accumulation", "weighted_words",
-                "weighted_short_row")
+                "weighted_short_row", "weighted_kernel")
 
 
 def _pow2_class(x: float) -> int:
