@@ -129,34 +129,29 @@ __device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint
     bool fine = true;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
-        unsigned long long nd[kLanesBatch];
-        DistSig cur[kLanesBatch];
+        unsigned long long nd[kLanesBatch], cd[kLanesBatch];
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
             const long long aj = a + (long long)j * step;
             y[j] = aj < ae ? __ldg(p.col + aj) : -1;
             nd[j] = aj < ae ? d + __ldg(p.wt + aj) : 0ull;
         }
+        // the heads' distances first (8 bytes each); the whole pair only
+        // for the few candidates that lower or tie
+#pragma unroll
+        for (int j = 0; j < kLanesBatch; ++j) cd[j] = y[j] >= 0 ? ds[y[j]].d : 0ull;
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
-            if (y[j] >= 0) {
-                cur[j] = ds[y[j]];
-            } else {
-                cur[j].d = 0ull;
-                cur[j].s = 0.0;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) {
-            if (y[j] < 0 || nd[j] > cur[j].d) continue;
+            if (y[j] < 0 || nd[j] > cd[j]) continue;
             DistSig *q = ds + y[j];
+            DistSig cur = *q;
             for (int it = 0;; ++it) {
-                if (nd[j] > cur[j].d) break;
-                const bool lower = nd[j] < cur[j].d;
+                if (nd[j] > cur.d) break;
+                const bool lower = nd[j] < cur.d;
                 DistSig nw;
                 nw.d = nd[j];
-                nw.s = lower ? sg : cur[j].s + sg;
-                if (cas_pair(q, cur[j], nw)) {
+                nw.s = lower ? sg : cur.s + sg;
+                if (cas_pair(q, cur, nw)) {
                     adds += 1;
                     if (lower) {
                         const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
