@@ -434,9 +434,9 @@ def run_gpu(args):
 
 
 def run_extras(args, bcd, dg22, g22, stream):
-    """Extra keys of the one-GPU line: the exact R-MAT 20 batch (one warm
-    and one timed call) and a short serving run on the resident R-MAT 22
-    graph."""
+    """Extra keys of the one-GPU line: the exact R-MAT 20 batch and a sampled
+    batch on the weighted R-MAT 20 (one warm and one timed call each), and a
+    short serving run on the resident R-MAT 22 graph."""
     import torch
     out = {}
     g, qs, specs = make_workload("rmat20_ef16_exact64")
@@ -454,6 +454,23 @@ def run_extras(args, bcd, dg22, g22, stream):
         "gteps": info["edges_traversed"] / wall / 1e9, "sources_in_union": info["sources_run"],
         "ms_traversal": info["ms_traversal"], "algorithmic_gbs": ab / (info["ms_traversal"] / 1000.0) / 1e9,
         "frac": ab / (info["ms_traversal"] / 1000.0) / 1e9 / peak, "bc_first": res[0]["bc"]}
+    dg.close()
+    # the weighted graph of rmat20_w255_exact32 with its 32 query vertices
+    # sampled (A-BCD eps 0.05, delta 0.1: T = 600), on the weighted source kernel
+    g, qs, _ = make_workload("rmat20_w255_exact32")
+    specs = [{"r": r, "kind": 1, "eps": 0.05, "delta": 0.1, "seed": 7} for r in qs]
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights, stream=stream.cuda_stream)
+    bcd.bc_batch(dg, specs)
+    torch.cuda.synchronize()
+    t = time.time()
+    res, info = bcd.bc_batch(dg, specs)
+    wall = time.time() - t
+    out["rmat20_w255_sampled32"] = {
+        "recipe": WORKLOADS["rmat20_w255_exact32"].replace("32 exact queries", "32 queries, A-BCD eps 0.05 delta 0.1 "
+                                                            "(T = 600) Philox seed 7"),
+        "queries_per_s": len(qs) / wall, "s_per_batch": wall, "gteps": info["edges_traversed"] / wall / 1e9,
+        "sources_in_union": info["sources_run"], "ms_traversal": info["ms_traversal"],
+        "weighted_kernel": bcd.bc_get_config(dg)["weighted_kernel"], "bc_first": res[0]["bc"]}
     dg.close()
     if args.serve_extra > 0:
         specs_s, draws, rvs = serve_workload(bcd, dg22, g22, args.serve_extra, args.serve_rv_max)

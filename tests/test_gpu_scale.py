@@ -287,6 +287,26 @@ def test_rmat20_weighted_vertex_scan(bcd, rmat20w):
     assert close(scan[0]["bc"], want) and close(push[0]["bc"], want), (scan[0]["bc"], push[0]["bc"], want)
 
 
+def test_rmat20_weighted_kernels_agree(bcd, rmat20w):
+    """Both weighted kernels at full size, each under the Eq. 4 pull and the
+    vertex scan: 96 draws (seed 5) on the vertex of largest in*out degree,
+    all four against the oracle on the same draws."""
+    g, og, dg, qs = rmat20w
+    top = int(gg.top_inout_vertices(g, 1)[0])
+    spec = {"r": top, "kind": bcd.BC_QUERY_APPROX_T, "T": 96, "seed": 5}
+    want = O.bc_approx(og, top, 96, 5, os.cpu_count() or 1)[0]
+    assert want > 0.0
+    try:
+        for kernel in (1, 2):
+            for acc in (1, 2):
+                bcd.bc_set_config(dg, weighted_kernel=kernel, accumulation=acc)
+                out, info = bcd.bc_batch(dg, [spec])
+                assert (info["scan_pairs"] > 0) == (acc == 2)
+                assert out[0]["status"] == 0 and close(out[0]["bc"], want), (kernel, acc, out[0]["bc"], want)
+    finally:
+        bcd.bc_set_config(dg, weighted_kernel=2, accumulation=1)
+
+
 def test_rmat20_weighted_multi_vertex_scan(bcd, rmat20w):
     """The weighted batch's query vertices in the giant component (seed 104)
     as one group under the default per-group choice (the vertex scan over

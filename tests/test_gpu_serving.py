@@ -74,6 +74,39 @@ def test_server_mix_equals_alone(setup):
             assert close(gres["bc"], O.bc_approx(og, s["r"], s["T"], s["seed"], 0)[0])
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_server_weighted_mix_equals_alone(setup, kernel):
+    """The same mix on the graph with weights 1..255 (seed 3), under the
+    weighted tile kernel (1) and the source kernel (2): every served result
+    equals the query alone, and spot checks equal the oracle."""
+    bcd, g, og, specs = setup
+    gw = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    ogw = O.Graph.from_csr(gw)
+    dg = bcd.bc_graph_create(gw.n, gw.offsets, gw.cols, gw.weights)
+    bcd.bc_set_config(dg, weighted_kernel=kernel)
+    sub = specs[:30]
+    want = [alone(bcd, dg, s) for s in sub]
+    srv = bcd.Server(dg, tiles_per_slice=2)
+    tickets = [srv.submit(s) for s in sub]
+    got = [None] * len(sub)
+    deadline = time.time() + 300
+    while any(x is None for x in got) and time.time() < deadline:
+        for i, t in enumerate(tickets):
+            if got[i] is None:
+                r = srv.poll(t, timeout_us=1000)
+                if r is not None:
+                    got[i] = r[0]
+    srv.close()
+    assert all(x is not None for x in got)
+    for s, gres, w in zip(sub, got, want):
+        assert gres["status"] == 0 and close(gres["bc"], w), (s, gres["bc"], w)
+    for s, gres in list(zip(sub, got))[:6]:
+        if s["kind"] == bcd.BC_QUERY_EXACT:
+            assert close(gres["bc"], O.bc_exact(ogw, s["r"], 0)[0])
+        elif s["kind"] == bcd.BC_QUERY_APPROX_T:
+            assert close(gres["bc"], O.bc_approx(ogw, s["r"], s["T"], s["seed"], 0)[0])
+
+
 def test_server_rejects_and_drains(setup):
     bcd, g, og, specs = setup
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols)

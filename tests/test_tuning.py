@@ -36,7 +36,7 @@ def test_table_roundtrip(tmp_path):
     def fake_tune(dg, specs, probe_T):
         calls["tune"] += 1
         return ({"tile_words": 2, "blocks_per_sm": 1, "chunk_arcs": 64, "pull_permille": -1, "accumulation": 4,
-                 "weighted_words": 1, "weighted_short_row": 32, "block_threads": 512},
+                 "weighted_words": 1, "weighted_short_row": 32, "weighted_kernel": 2, "block_threads": 512},
                 {"candidates": 9, "probe_queries": 2, "ms_default": 10.0, "ms_best": 8.0})
 
     def fake_set(dg, **cfg):
