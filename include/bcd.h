@@ -400,11 +400,12 @@ void bc_server_destroy(bc_server *srv);
  *                  (the 64 * weighted_words sources of a tile settle their
  *                  (vertex, source) pairs together, one grid-wide barrier
  *                  per distance value); 2 (default) the source kernel: each
- *                  block takes one source at a time and settles its
+ *                  block (1024 threads, one per SM; block_threads does not
+ *                  apply) takes one source at a time and settles its
  *                  distances with block barriers only, so blocks never wait
  *                  on one another (per block: 20 bytes per vertex plus the
  *                  bucket ring; as many blocks as fit in half of the free
- *                  device memory, up to the resident maximum). Both give
+ *                  device memory, up to one per SM). Both give
  *                  the same distances and sigma; dependencies agree up to
  *                  fp64 summation order. The traversal rooted at the query
  *                  vertices of the vertex scan, and bc_spd_probe, always
@@ -438,8 +439,9 @@ bc_status bc_get_config(const bc_graph *g, bc_config *cfg);
  * of the batch, second of two runs) is kept:
  *   unweighted: tile_words 2, 4, 8; blocks_per_sm 1, 2; chunk_arcs 64, 128, 256;
  *               pull_permille -1, 200; accumulation 1, 4;
- *   weighted:   weighted_words 2, 4, 8; weighted_short_row 16, 32, 64;
- *               chunk_arcs 64, 128, 256; accumulation 1, 4.
+ *   weighted:   weighted_kernel 1, 2; weighted_words 2, 4, 8;
+ *               weighted_short_row 16, 32, 64; chunk_arcs 64, 128, 256;
+ *               accumulation 1, 4.
  * Candidates that do not fit in device memory are skipped. The winner is
  * applied to g and written to *best; rep (may be NULL) receives the number
  * of candidates timed and the probe times of the starting and the chosen
