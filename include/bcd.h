@@ -66,7 +66,9 @@ typedef enum { BC_MEM_HOST = 0, BC_MEM_DEVICE = 1 } bc_mem_kind;
  *   cols[m]          int32 heads; within each row strictly increasing
  *                    (sorted, which also rules out repeated arcs), no
  *                    self-loop;
- *   weights[m]       uint32 positive arc lengths, or NULL for an
+ *   weights[m]       uint32 positive arc lengths of at most 4095 (the
+ *                    weighted kernels settle distances in Dial's order
+ *                    over a ring of 4096 distance slots), or NULL for an
  *                    unweighted graph (every arc has length 1).
  * mem_kind tells whether the three pointers are host or device memory.
  * stream is a cudaStream_t (NULL: the legacy default stream).
@@ -88,8 +90,8 @@ typedef struct bc_graph bc_graph;
  * graph R(G) there (Section 4.1, Def. 2). The caller keeps ownership of its
  * arrays. Errors: BC_E_INVALID_ARG (n <= 0, m < 0, NULL pointer, offsets
  * not monotone, head out of range), BC_E_INVALID_GRAPH (self-loop, row not
- * strictly increasing, weight 0), BC_E_OOM, BC_E_CUDA. *out is set only on
- * success.
+ * strictly increasing, weight 0 or above 4095), BC_E_OOM, BC_E_CUDA. *out
+ * is set only on success.
  */
 bc_status bc_graph_create(const bc_graph_desc *desc, bc_graph **out);
 

@@ -313,6 +313,9 @@ bc_status bc_graph_create(const bc_graph_desc *d, bc_graph **out) {
         ce = cudaStreamSynchronize(s);
         dev_free(d_mx);
         if (ce != cudaSuccess) return fail(cuda_error(ce, "max weight"));
+        if (hmx > 4095)
+            return fail(set_error(BC_E_INVALID_GRAPH, "bc_graph_create: weights must be at most 4095 (the distance "
+                                                      "ring of the weighted kernels has 4096 slots)"));
         g->max_weight = hmx;
     }
 

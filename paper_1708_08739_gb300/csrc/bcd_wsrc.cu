@@ -777,9 +777,10 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
     if (per_sm < 1) return set_error(BC_E_INTERNAL, "weighted source kernel cannot be resident");
     if (ws.sbcap == 0) {
         // queued vertices of one distance of one source: a few times the
-        // average vertices per distance value; grown on overflow
-        int64_t b = 8192;
-        while (b < 4 * (int64_t)g->n / R && b < ((int64_t)1 << 30)) b *= 2;
+        // average vertices per distance value, and at least 2^21 entries
+        // over the whole ring (8 MB); grown on overflow
+        int64_t b = 64;
+        while ((b < 4 * (int64_t)g->n / R || b * R < ((int64_t)1 << 21)) && b < ((int64_t)1 << 30)) b *= 2;
         ws.sbcap = b;
         ws.schcap = 16384;
         ws.smaxlev = 8192;

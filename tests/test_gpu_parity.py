@@ -378,6 +378,29 @@ def test_weighted_rmat_small(bcd, cfg):
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("lo", [1, 4000])
+def test_weighted_largest_weights(bcd, kernel, lo):
+    """Weights up to 4095, the largest the library takes (a ring of 4,096
+    distance slots): uniform in [1, 4095], or in [4000, 4095] where a
+    distance value rarely repeats; exact scores of a batch against the
+    oracle."""
+    g = gg.erdos_renyi(600, 4000, 21)
+    g = g.with_weights(gg.uniform_weights(g.m, lo, 4095, 8))
+    og = O.Graph.from_csr(g)
+    dg = make(bcd, g, weighted_kernel=kernel)
+    qs = gg.random_vertices(g.n, 10, 104).tolist()
+    out, _ = bcd.bc_batch(dg, [{"r": r} for r in qs])
+    for r, o in zip(qs, out):
+        want = O.bc_exact(og, r, 0)[0]
+        assert o["status"] == 0 and close(o["bc"], want), (r, o["bc"], want)
+    with pytest.raises(bcd.BCError) as e:
+        w = g.weights.copy()
+        w[0] = 4096
+        bcd.bc_graph_create(g.n, g.offsets, g.cols, w)
+    assert e.value.status == bcd.BC_E_INVALID_GRAPH
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
 def test_weighted_growth_paths_closed_forms(bcd, kernel):
     """Capacities that start too small and grow on the rerun.
     - A directed path of 10,000 vertices with weights 1..2 has about 15,000
