@@ -202,9 +202,12 @@ typedef struct {
     int32_t grid_blocks;      /* blocks of the persistent traversal launch */
     double ms_traversal;      /* CUDA-event time of the batched traversal launches */
     int64_t reached_pairs;    /* sum over sources s of |V_s| (vertices s reaches) */
-    int64_t tight_pairs;      /* sum over sources s of the arcs of s's SPD */
+    int64_t tight_pairs;      /* sum over sources s of the arcs of s's SPD (weighted
+                                 source kernel: the sigma offers that took effect, which
+                                 also counts ties a shorter path later replaced) */
     int64_t arc_visits;       /* arcs scanned by the traversal, both passes */
-    int64_t union_vertices;   /* sum over tiles of vertices any tile source reaches */
+    int64_t union_vertices;   /* sum over tiles of vertices any tile source reaches
+                                 (weighted source kernel: over each launch) */
     int64_t union_arcs;       /* sum over tiles of the out-arcs of those vertices */
     int64_t scan_pairs;       /* accumulation 2: (t, s) pairs with the query vertex on a
                                  shortest s-t path (the terms of the vertex scan) */
