@@ -235,6 +235,7 @@ struct bcd_workspace {
     // weighted source kernel (one source per block): per-block state
     int32_t sblocks = 0;                   // blocks the state is sized for
     unsigned long long *sds = nullptr;     // [sblocks * n * 2]: (distance, sigma) of each vertex
+    uint32_t *stb = nullptr;               // [sblocks * (m + 31) / 32]: tight-candidate arc bits
     int32_t *shv = nullptr;                // [sblocks * n]
     int32_t *slstart = nullptr;            // [sblocks * smaxlev]
     unsigned long long *sldist = nullptr;  // [sblocks * smaxlev]

@@ -79,6 +79,8 @@ struct SrcParams {
     uint32_t *bk;               // [blocks * ring * bcap] queued vertices, circular per slot
     Chunk *ch;                  // [blocks * chcap] long-row chunks of one level
     double *part;               // [blocks * chcap] backward chunk sums
+    uint32_t *tb;               // [blocks * tbw] one bit per arc: its offer took effect (Eq. 4 launches)
+    int64_t tbw;                // words per block: (m + 31) / 32
     double *sdep;               // [nsrc * 64]
     uint32_t *sflag;            // [nsrc] sigma >= 2^53 seen
     unsigned long long *next;   // source hand-out
@@ -125,11 +127,14 @@ constexpr int kCasTries = 1 << 16;  // a pair changed under us this often: give 
 
 // Offers out-arcs a, a + step, ... < ae of a vertex settled at distance d
 // with path count sg: lowers a head's distance (and queues it) or adds sg to
-// its count when the candidate ties. Returns false if a pair kept changing
-// past kCasTries attempts.
+// its count when the candidate ties. With tb (Eq. 4 launches), an offer that
+// took effect also sets its arc's bit: every tight arc gets one (its offer
+// of the final distance always takes effect), and arcs whose offer a shorter
+// path replaced keep a stale bit that the backward's check drops. Returns
+// false if a pair kept changing past kCasTries attempts.
 __device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint32_t *bk, uint32_t *s_cnt,
-                                          int64_t bcap, int R, unsigned long long d, double sg, long long a,
-                                          long long ae, int step, unsigned long long &adds) {
+                                          uint32_t *tb, int64_t bcap, int R, unsigned long long d, double sg,
+                                          long long a, long long ae, int step, unsigned long long &adds) {
     bool fine = true;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
@@ -157,6 +162,10 @@ __device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint
                 nw.s = lower ? sg : cur.s + sg;
                 if (cas_pair(q, cur, nw)) {
                     adds += 1;
+                    if (tb) {
+                        const long long aj = a + (long long)j * step;
+                        atomicOr(tb + (aj >> 5), 1u << (aj & 31));
+                    }
                     if (lower) {
                         const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
                         const uint32_t pos = atomicAdd(&s_cnt[slot], 1u);
@@ -175,9 +184,11 @@ __device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint
 }
 
 // Sum of c(y) over the tight out-arcs (y at distance d + w(v, y)) among a,
-// a + step, ... < ae of a vertex at distance d.
-__device__ __forceinline__ double src_pull_c(const TravParams &p, const DistSig *ds, unsigned long long d, long long a,
-                                             long long ae, int step) {
+// a + step, ... < ae of a vertex at distance d. Only arcs whose bit the
+// forward set can be tight; the others are skipped without reading their
+// head.
+__device__ __forceinline__ double src_pull_c(const TravParams &p, const DistSig *ds, const uint32_t *tb,
+                                             unsigned long long d, long long a, long long ae, int step) {
     double acc = 0.0;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
@@ -186,13 +197,20 @@ __device__ __forceinline__ double src_pull_c(const TravParams &p, const DistSig 
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
             const long long aj = a + (long long)j * step;
-            ok[j] = aj < ae;
+            ok[j] = aj < ae && ((tb[aj >> 5] >> (aj & 31)) & 1u);
             y[j] = ok[j] ? __ldg(p.col + aj) : 0;
             want[j] = ok[j] ? d + __ldg(p.wt + aj) : 0ull;
         }
         DistSig v[kLanesBatch];
 #pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) v[j] = ds[y[j]];
+        for (int j = 0; j < kLanesBatch; ++j) {
+            if (ok[j]) {
+                v[j] = ds[y[j]];
+            } else {
+                v[j].d = ~0ull;
+                v[j].s = 0.0;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j)
             if (ok[j] && v[j].d == want[j]) acc += v[j].s;
@@ -266,6 +284,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
     uint32_t *bk = q.bk + (size_t)blockIdx.x * (size_t)R * (size_t)bcap;
     Chunk *chs = q.ch + (size_t)blockIdx.x * (size_t)q.chcap;
     double *part = q.part + (size_t)blockIdx.x * (size_t)q.chcap;
+    uint32_t *tb = p.mode == kModeSpd ? q.tb + (size_t)blockIdx.x * (size_t)q.tbw : nullptr;
     SrcStats st;
     unsigned long long ns_fwd = 0, ns_bwd = 0, ns_other = 0, t_mark = 0;
     unsigned long long lev_max = 0;
@@ -390,7 +409,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     }
                     if (ok && re - rb <= p.wshort) {
                         if (lead) st.arcs += (unsigned long long)(re - rb);
-                        if (!src_relax(p, ds, bk, s_cnt, bcap, R, d, px.s, rb + rl, re, lpp, st.tight)) {
+                        if (!src_relax(p, ds, bk, s_cnt, tb, bcap, R, d, px.s, rb + rl, re, lpp, st.tight)) {
                             s_err = 1;
                             set_err(p.ctr, kDevTimeout);
                         }
@@ -422,7 +441,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                 for (int c = warp; c < nch; c += nwarps) {
                     const Chunk ch = load_chunk(&chs[c]);
                     const double sg = ds[ch.v].s;
-                    if (!src_relax(p, ds, bk, s_cnt, bcap, R, d, sg, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight)) {
+                    if (!src_relax(p, ds, bk, s_cnt, tb, bcap, R, d, sg, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight)) {
                         s_err = 1;
                         set_err(p.ctr, kDevTimeout);
                     }
@@ -552,7 +571,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     }
                     const bool shortrow = ok && re - rb <= p.wshort;
                     double acc = 0.0;
-                    if (shortrow) acc = src_pull_c(p, ds, dk, rb + rl, re, lpp);
+                    if (shortrow) acc = src_pull_c(p, ds, tb, dk, rb + rl, re, lpp);
                     acc = sum_lanes(acc, lpp);
                     if (shortrow && lead) {
                         src_finalize(p, ds, need, s_dep, v, acc);
@@ -581,7 +600,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                 if (nch > 0) {
                     for (int c = warp; c < nch; c += nwarps) {
                         const Chunk ch = load_chunk(&chs[c]);
-                        const double v = sum_warp(src_pull_c(p, ds, dk, ch.a0 + lane, ch.a0 + ch.na, 32));
+                        const double v = sum_warp(src_pull_c(p, ds, tb, dk, ch.a0 + lane, ch.a0 + ch.na, 32));
                         if (lane == 0) part[c] = v;
                         if (lane < ch.na) st.arcs += (unsigned long long)((ch.na - lane + 31) / 32);
                     }
@@ -603,10 +622,16 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
         if (tid < 64 && ((need >> tid) & 1ull)) q.sdep[(size_t)si * 64 + tid] = s_dep[tid];
         if (tid == 0) q.sflag[si] = (uint32_t)s_flag;
         for (int e = tid; e < nh; e += bd) {
+            const int x = hv[e];
             DistSig z;
             z.d = ~0ull;
             z.s = 0.0;
-            ds[hv[e]] = z;
+            ds[x] = z;
+            if (tb) {
+                const long long rb = __ldg(p.off + x), re = __ldg(p.off + x + 1);
+                if (re > rb)
+                    for (long long w = rb >> 5; w <= (re - 1) >> 5; ++w) tb[w] = 0u;
+            }
         }
         if (tid == 0) {
             const unsigned long long t = global_ns();
@@ -674,8 +699,9 @@ __global__ void wsrc_tile_sums(TravParams p, const double *sdep, const uint32_t 
 }
 
 // Bytes of per-block state for a graph of n vertices.
-size_t src_block_bytes(int64_t n, int R, int64_t bcap, int64_t maxlev, int64_t chcap) {
-    return (size_t)n * (16 + 4) + (size_t)R * (size_t)bcap * 4 + (size_t)maxlev * 12 + (size_t)chcap * (32 + 8);
+size_t src_block_bytes(int64_t n, int64_t m, int R, int64_t bcap, int64_t maxlev, int64_t chcap) {
+    return (size_t)n * (16 + 4) + (size_t)((m + 31) / 32) * 4 + (size_t)R * (size_t)bcap * 4 + (size_t)maxlev * 12 +
+           (size_t)chcap * (32 + 8);
 }
 
 // Every pair unreached: distance all ones, sigma zero.
@@ -697,6 +723,7 @@ bc_status clear_src_pairs(bc_graph *g) {
 
 void free_src_arrays(bcd_workspace &ws) {
     dev_free(ws.sds);
+    dev_free(ws.stb);
     dev_free(ws.shv);
     dev_free(ws.slstart);
     dev_free(ws.sldist);
@@ -714,6 +741,8 @@ bc_status alloc_src_arrays(bc_graph *g, int blocks) {
     const size_t B = (size_t)blocks;
     const size_t n = (size_t)g->n;
     BCD_TRY(dev_alloc(&ws.sds, 2 * B * n));
+    BCD_TRY(dev_alloc(&ws.stb, B * (size_t)((g->m + 31) / 32)));
+    BCD_CUDA(cudaMemsetAsync(ws.stb, 0, sizeof(uint32_t) * B * (size_t)((g->m + 31) / 32), g->stream));
     BCD_TRY(dev_alloc(&ws.shv, B * n));
     BCD_TRY(dev_alloc(&ws.slstart, B * (size_t)ws.smaxlev));
     BCD_TRY(dev_alloc(&ws.sldist, B * (size_t)ws.smaxlev));
@@ -728,6 +757,7 @@ bc_status reset_src_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (!ws.sds) return BC_OK;
     BCD_TRY(clear_src_pairs(g));
+    BCD_CUDA(cudaMemsetAsync(ws.stb, 0, sizeof(uint32_t) * (size_t)ws.sblocks * (size_t)((g->m + 31) / 32), g->stream));
     if (ws.tag) BCD_CUDA(cudaMemsetAsync(ws.tag, 0xff, sizeof(int32_t) * (size_t)g->n, g->stream));
     return BC_OK;
 }
@@ -789,8 +819,8 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
     {
         size_t fr = 0, tot = 0;
         BCD_CUDA(cudaMemGetInfo(&fr, &tot));
-        const size_t have = ws.sblocks > 0 ? src_block_bytes(g->n, R, ws.sbcap, ws.smaxlev, ws.schcap) * ws.sblocks : 0;
-        const size_t per = src_block_bytes(g->n, R, ws.sbcap, ws.smaxlev, ws.schcap);
+        const size_t have = ws.sblocks > 0 ? src_block_bytes(g->n, g->m, R, ws.sbcap, ws.smaxlev, ws.schcap) * ws.sblocks : 0;
+        const size_t per = src_block_bytes(g->n, g->m, R, ws.sbcap, ws.smaxlev, ws.schcap);
         const size_t budget = (fr + have) / 2;
         blocks = (int)std::min<size_t>((size_t)blocks, budget / per);
         if (blocks < 1) return set_error(BC_E_OOM, "weighted source kernel: no room for one block's state");
@@ -827,6 +857,8 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         q.bk = ws.sbk;
         q.ch = ws.sch;
         q.part = ws.spart;
+        q.tb = ws.stb;
+        q.tbw = (g->m + 31) / 32;
         q.sdep = ws.sdep;
         q.sflag = ws.sflag;
         q.next = ws.snext;
@@ -886,7 +918,7 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         if (p.qflags) BCD_CUDA(cudaMemsetAsync(p.qflags, 0, sizeof(uint32_t) * 64, g->stream));
         if (c.err == kDevTimeout) return set_error(BC_E_TIMEOUT, "weighted source kernel: a source ran past the time limit");
         if (c.err == kDevCancelled) return set_error(BC_E_CANCELLED, "traversal: cancelled by bc_cancel");
-        const size_t before = (size_t)ws.sblocks * src_block_bytes(g->n, R, ws.sbcap, ws.smaxlev, ws.schcap);
+        const size_t before = (size_t)ws.sblocks * src_block_bytes(g->n, g->m, R, ws.sbcap, ws.smaxlev, ws.schcap);
         if (c.err == kDevBucketOverflow) {
             if (ws.sbcap >= ((int64_t)1 << 30)) return set_error(BC_E_OOM, "bucket ring: too many queued vertices at one distance");
             ws.sbcap *= 2;
@@ -902,7 +934,7 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         // grow, within half of the memory free besides the current state
         size_t fr = 0, tot = 0;
         BCD_CUDA(cudaMemGetInfo(&fr, &tot));
-        const size_t per = src_block_bytes(g->n, R, ws.sbcap, ws.smaxlev, ws.schcap);
+        const size_t per = src_block_bytes(g->n, g->m, R, ws.sbcap, ws.smaxlev, ws.schcap);
         const int nb = (int)std::min<size_t>((size_t)ws.sblocks, ((fr + before) / 2) / per);
         if (nb < 1) {
             free_src_arrays(ws);
