@@ -23,6 +23,7 @@ enum DevErr : int32_t {
     kDevLevelOverflow = 5,
     kDevBucketOverflow = 6,
     kDevCancelled = 7,
+    kDevWide = 8,  // weighted source kernel: a count or distance needs the 16-byte pairs
 };
 
 // Per-launch control block of the persistent traversal kernel.
@@ -236,6 +237,8 @@ struct bcd_workspace {
     int32_t sblocks = 0;                   // blocks the state is sized for
     unsigned long long *sds = nullptr;     // [sblocks * n * 2]: (distance, sigma) of each vertex
     uint32_t *stb = nullptr;               // [sblocks * (m + 31) / 32]: tight-candidate arc bits
+    int32_t slayout = 0;                   // how sds is cleared: 1 16-byte pairs, 2 8-byte words
+    bool swide = false;                    // a narrow launch overflowed: 16-byte pairs from now on
     int32_t *shv = nullptr;                // [sblocks * n]
     int32_t *slstart = nullptr;            // [sblocks * smaxlev]
     unsigned long long *sldist = nullptr;  // [sblocks * smaxlev]

@@ -125,17 +125,100 @@ __device__ __forceinline__ bool cas_pair(DistSig *p, DistSig &expect, const Dist
 
 constexpr int kCasTries = 1 << 16;  // a pair changed under us this often: give up (never seen)
 
+// Outcome of one offer to a head's pair.
+enum Offer : int { kOfferNone = 0, kOfferTie = 1, kOfferLower = 2, kOfferStuck = -1, kOfferWide = -2 };
+
+// Wide layout: 16-byte (distance, sigma) pairs, sigma in fp64 (the Eq. 4
+// pass stores c there). Needed for Eq. 4 launches and for counts of 2^40 and
+// more.
+struct WidePairs {
+    static constexpr bool kWide = true;
+    static constexpr unsigned long long kUnreached = ~0ull;
+    DistSig *ds;
+    __device__ __forceinline__ unsigned long long dist(int v) const { return ds[v].d; }
+    __device__ __forceinline__ void get(int v, unsigned long long &d, double &sg) const {
+        const DistSig x = ds[v];
+        d = x.d;
+        sg = x.s;
+    }
+    __device__ __forceinline__ void seed(int v) const {
+        DistSig x;
+        x.d = 0ull;
+        x.s = 1.0;
+        ds[v] = x;
+    }
+    __device__ __forceinline__ void clear(int v) const {
+        DistSig x;
+        x.d = ~0ull;
+        x.s = 0.0;
+        ds[v] = x;
+    }
+    __device__ __forceinline__ int offer(int v, unsigned long long nd, double sg) const {
+        DistSig *q = ds + v;
+        DistSig cur = *q;
+        for (int it = 0; it < kCasTries; ++it) {
+            if (nd > cur.d) return kOfferNone;
+            const bool lower = nd < cur.d;
+            DistSig nw;
+            nw.d = nd;
+            nw.s = lower ? sg : cur.s + sg;
+            if (cas_pair(q, cur, nw)) return lower ? kOfferLower : kOfferTie;
+        }
+        return kOfferStuck;
+    }
+};
+
+// Narrow layout: one 8-byte word per vertex, the distance in bits 0-23
+// (2^24 - 1: unreached) and sigma as an integer in bits 24-63, changed by a
+// 64-bit compare-and-swap. Half the footprint of the wide pairs, so more of
+// the block's state stays in L2. A distance of 2^24 - 1 or more, or a count
+// of 2^40 or more, asks for the wide layout (the launch reruns with it).
+struct NarrowPairs {
+    static constexpr bool kWide = false;
+    static constexpr unsigned long long kDistMask = (1ull << 24) - 1;
+    static constexpr unsigned long long kUnreached = kDistMask;
+    static constexpr unsigned long long kSigLimit = 1ull << 40;
+    unsigned long long *w;
+    __device__ __forceinline__ unsigned long long dist(int v) const { return w[v] & kDistMask; }
+    __device__ __forceinline__ void get(int v, unsigned long long &d, double &sg) const {
+        const unsigned long long x = w[v];
+        d = x & kDistMask;
+        sg = (double)(x >> 24);
+    }
+    __device__ __forceinline__ void seed(int v) const { w[v] = 1ull << 24; }
+    __device__ __forceinline__ void clear(int v) const { w[v] = kDistMask; }
+    __device__ __forceinline__ int offer(int v, unsigned long long nd, double sg) const {
+        if (nd >= kDistMask) return kOfferWide;
+        const unsigned long long si = (unsigned long long)sg;  // an integer below 2^40
+        unsigned long long cur = w[v];
+        for (int it = 0; it < kCasTries; ++it) {
+            const unsigned long long cd = cur & kDistMask;
+            if (nd > cd) return kOfferNone;
+            const bool lower = nd < cd;
+            const unsigned long long ns = lower ? si : (cur >> 24) + si;
+            if (ns >= kSigLimit) return kOfferWide;
+            const unsigned long long nw = nd | (ns << 24);
+            const unsigned long long old = atomicCAS(w + v, cur, nw);
+            if (old == cur) return lower ? kOfferLower : kOfferTie;
+            cur = old;
+        }
+        return kOfferStuck;
+    }
+};
+
 // Offers out-arcs a, a + step, ... < ae of a vertex settled at distance d
 // with path count sg: lowers a head's distance (and queues it) or adds sg to
 // its count when the candidate ties. With tb (Eq. 4 launches), an offer that
 // took effect also sets its arc's bit: every tight arc gets one (its offer
 // of the final distance always takes effect), and arcs whose offer a shorter
-// path replaced keep a stale bit that the backward's check drops. Returns
-// false if a pair kept changing past kCasTries attempts.
-__device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint32_t *bk, uint32_t *s_cnt,
-                                          uint32_t *tb, int64_t bcap, int R, unsigned long long d, double sg,
-                                          long long a, long long ae, int step, unsigned long long &adds) {
-    bool fine = true;
+// path replaced keep a stale bit that the backward's check drops. Returns 0,
+// or the device error to raise (a pair that kept changing, a count or
+// distance the narrow layout cannot hold).
+template <class PairT>
+__device__ __forceinline__ int src_relax(const TravParams &p, const PairT &P, uint32_t *bk, uint32_t *s_cnt,
+                                         uint32_t *tb, int64_t bcap, int R, unsigned long long d, double sg,
+                                         long long a, long long ae, int step, unsigned long long &adds) {
+    int err = 0;
     for (; a < ae; a += kLanesBatch * step) {
         int y[kLanesBatch];
         unsigned long long nd[kLanesBatch], cd[kLanesBatch];
@@ -145,42 +228,33 @@ __device__ __forceinline__ bool src_relax(const TravParams &p, DistSig *ds, uint
             y[j] = aj < ae ? __ldg(p.col + aj) : -1;
             nd[j] = aj < ae ? d + __ldg(p.wt + aj) : 0ull;
         }
-        // the heads' distances first (8 bytes each); the whole pair only
-        // for the few candidates that lower or tie
+        // the heads' distances first; the compare-and-swap only for the few
+        // candidates that lower or tie
 #pragma unroll
-        for (int j = 0; j < kLanesBatch; ++j) cd[j] = y[j] >= 0 ? ds[y[j]].d : 0ull;
+        for (int j = 0; j < kLanesBatch; ++j) cd[j] = y[j] >= 0 ? P.dist(y[j]) : 0ull;
 #pragma unroll
         for (int j = 0; j < kLanesBatch; ++j) {
             if (y[j] < 0 || nd[j] > cd[j]) continue;
-            DistSig *q = ds + y[j];
-            DistSig cur = *q;
-            for (int it = 0;; ++it) {
-                if (nd[j] > cur.d) break;
-                const bool lower = nd[j] < cur.d;
-                DistSig nw;
-                nw.d = nd[j];
-                nw.s = lower ? sg : cur.s + sg;
-                if (cas_pair(q, cur, nw)) {
-                    adds += 1;
-                    if (tb) {
-                        const long long aj = a + (long long)j * step;
-                        atomicOr(tb + (aj >> 5), 1u << (aj & 31));
-                    }
-                    if (lower) {
-                        const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
-                        const uint32_t pos = atomicAdd(&s_cnt[slot], 1u);
-                        bk[(size_t)slot * (size_t)bcap + (pos & (uint32_t)(bcap - 1))] = (uint32_t)y[j];
-                    }
-                    break;
+            const int r = P.offer(y[j], nd[j], sg);
+            if (r > 0) {
+                adds += 1;
+                if (tb) {
+                    const long long aj = a + (long long)j * step;
+                    atomicOr(tb + (aj >> 5), 1u << (aj & 31));
                 }
-                if (it >= kCasTries) {
-                    fine = false;
-                    break;
+                if (r == kOfferLower) {
+                    const int slot = (int)(nd[j] & (unsigned long long)(R - 1));
+                    const uint32_t pos = atomicAdd(&s_cnt[slot], 1u);
+                    bk[(size_t)slot * (size_t)bcap + (pos & (uint32_t)(bcap - 1))] = (uint32_t)y[j];
                 }
+            } else if (r == kOfferStuck) {
+                err = kDevTimeout;
+            } else if (r == kOfferWide) {
+                err = kDevWide;
             }
         }
     }
-    return fine;
+    return err;
 }
 
 // Sum of c(y) over the tight out-arcs (y at distance d + w(v, y)) among a,
@@ -256,6 +330,7 @@ __device__ __forceinline__ void src_finalize(const TravParams &p, DistSig *ds, u
     }
 }
 
+template <class PairT>
 __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcParams q) {
     extern __shared__ uint32_t s_ring[];  // [2 * R]: queued, then consumed, per slot
     __shared__ int32_t s_ql[64];          // level at which query vertex q settled for this source
@@ -277,7 +352,12 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
     uint32_t *s_cnt = s_ring;
     uint32_t *s_base = s_ring + R;
     const size_t boff = (size_t)blockIdx.x * (size_t)q.n;
-    DistSig *ds = q.ds + boff;
+    DistSig *ds = q.ds + boff;  // wide pairs (Eq. 4 reads and writes them directly)
+    PairT P;
+    if constexpr (PairT::kWide)
+        P.ds = ds;
+    else
+        P.w = reinterpret_cast<unsigned long long *>(q.ds) + boff;
     int32_t *hv = q.hv + boff;
     int32_t *lstart = q.lstart + (size_t)blockIdx.x * (size_t)q.maxlev;
     unsigned long long *ldist = q.ldist + (size_t)blockIdx.x * (size_t)q.maxlev;
@@ -324,8 +404,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
         if (v0 < 0) continue;
         const uint64_t need = __ldg(p.need + v0);
         if (tid == 0) {
-            ds[v0].d = 0ull;
-            ds[v0].s = 1.0;
+            P.seed(v0);
             bk[0] = (uint32_t)v0;  // slot 0, position 0
             s_cnt[0] = 1u;
         }
@@ -372,14 +451,13 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                 for (long long gi = warp; gi < ngroups; gi += nwarps) {
                     const long long ii = gi * per + sub;
                     int x = 0;
-                    DistSig px;
-                    px.d = ~0ull;
-                    px.s = 0.0;
+                    unsigned long long xd = PairT::kUnreached;
+                    double xs = 0.0;
                     if (ii < (long long)cnt) {
                         x = (int)bks[(b0 + (uint32_t)ii) & (uint32_t)(bcap - 1)];
-                        px = ds[x];
+                        P.get(x, xd, xs);
                     }
-                    const bool ok = px.d == d;
+                    const bool ok = xd == d;
                     const unsigned am = __ballot_sync(kFull, ok && lead);
                     if (am == 0u) continue;
                     int eb = 0;
@@ -395,8 +473,8 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                         hv[e] = x;
                         st.reached += 1;
                         st.edges += (unsigned long long)(re - rb);
-                        if (px.s >= kSrcTwo53) s_flag = 1;
-                        if (atomicCAS(&p.tag[x], -1, 0) == -1) {
+                        if (xs >= kSrcTwo53) s_flag = 1;
+                        if (*(volatile const int32_t *)(p.tag + x) == -1 && atomicCAS(&p.tag[x], -1, 0) == -1) {
                             st.vb += 1;
                             st.eb += (unsigned long long)(re - rb);
                         }
@@ -409,9 +487,10 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     }
                     if (ok && re - rb <= p.wshort) {
                         if (lead) st.arcs += (unsigned long long)(re - rb);
-                        if (!src_relax(p, ds, bk, s_cnt, tb, bcap, R, d, px.s, rb + rl, re, lpp, st.tight)) {
+                        const int er = src_relax(p, P, bk, s_cnt, tb, bcap, R, d, xs, rb + rl, re, lpp, st.tight);
+                        if (er) {
                             s_err = 1;
-                            set_err(p.ctr, kDevTimeout);
+                            set_err(p.ctr, er);
                         }
                     } else if (ok && lead) {
                         const int nout = (int)((re - rb + CH - 1) / CH);
@@ -440,10 +519,13 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
             if (nch > 0) {
                 for (int c = warp; c < nch; c += nwarps) {
                     const Chunk ch = load_chunk(&chs[c]);
-                    const double sg = ds[ch.v].s;
-                    if (!src_relax(p, ds, bk, s_cnt, tb, bcap, R, d, sg, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight)) {
+                    unsigned long long cdv;
+                    double sg;
+                    P.get(ch.v, cdv, sg);
+                    const int er = src_relax(p, P, bk, s_cnt, tb, bcap, R, d, sg, ch.a0 + lane, ch.a0 + ch.na, 32, st.tight);
+                    if (er) {
                         s_err = 1;
-                        set_err(p.ctr, kDevTimeout);
+                        set_err(p.ctr, er);
                     }
                     if (lane < ch.na) st.arcs += (unsigned long long)((ch.na - lane + 31) / 32);
                 }
@@ -470,16 +552,19 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
             // delta_s.(r) = sigma_sr * sum over settled t with d(r, t) >= 1 and
             // d(s, r) + d(r, t) = d(s, t) of sigma_rt / sigma_st
             const int r = p.vroot;
-            const DistSig pr = ds[r];
-            const unsigned long long dsr = pr.d;
+            unsigned long long dsr;
+            double ssr;
+            P.get(r, dsr, ssr);
             double acc = 0.0;
-            if (dsr != ~0ull && need) {
+            if (dsr != PairT::kUnreached && need) {
                 for (int e = tid; e < nh; e += bd) {
                     const int t = hv[e];
                     const unsigned long long rd = p.rdist[t];
-                    const DistSig pt = ds[t];
-                    if (rd == 0ull || rd >= pt.d || dsr + rd != pt.d) continue;
-                    acc += p.rsig[t] / pt.s;
+                    unsigned long long dt;
+                    double sst;
+                    P.get(t, dt, sst);
+                    if (rd == 0ull || rd >= dt || dsr + rd != dt) continue;
+                    acc += p.rsig[t] / sst;
                     st.pairs += 1;
                 }
             }
@@ -489,7 +574,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
             if (tid == 0) {
                 double sum = 0.0;
                 for (int w = 0; w < nwarps; ++w) sum += s_red[w];
-                const double dv = dsr != ~0ull ? pr.s * sum : 0.0;
+                const double dv = dsr != PairT::kUnreached ? ssr * sum : 0.0;
                 uint64_t y = need;
                 while (y) {
                     const int qq = __ffsll((long long)y) - 1;
@@ -509,19 +594,19 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     cols |= 1ull << p.qcol[qq];
                 }
             }
-            for (int c = tid; c < 64; c += bd) s_cd[c] = ((cols >> c) & 1ull) ? ds[p.croot[c]].d : ~0ull;
+            for (int c = tid; c < 64; c += bd) s_cd[c] = ((cols >> c) & 1ull) ? P.dist(p.croot[c]) : PairT::kUnreached;
             __syncthreads();
             for (int e = tid; e < nh; e += bd) {
                 const int t = hv[e];
-                const DistSig pt = ds[t];
-                const unsigned long long dt = pt.d;
-                const double sst = pt.s;
+                unsigned long long dt;
+                double sst;
+                P.get(t, dt, sst);
                 uint64_t y = cols;
                 while (y) {
                     const int c = __ffsll((long long)y) - 1;
                     y &= y - 1;
                     const unsigned long long dc = s_cd[c];
-                    if (dc == ~0ull) continue;
+                    if (dc == PairT::kUnreached) continue;
                     const unsigned long long rd = p.rdistq[(size_t)t * 64 + c];
                     if (rd == 0ull || rd >= dt || dc + rd != dt) continue;
                     atomicAdd(&s_msum[c], p.rsigq[(size_t)t * 64 + c] / sst);
@@ -535,10 +620,13 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     const int qq = __ffsll((long long)y) - 1;
                     y &= y - 1;
                     const int c = p.qcol[qq];
-                    s_dep[qq] = s_cd[c] != ~0ull ? ds[p.croot[c]].s * s_msum[c] : 0.0;
+                    unsigned long long dcr;
+                    double scr;
+                    P.get(p.croot[c], dcr, scr);
+                    s_dep[qq] = s_cd[c] != PairT::kUnreached ? scr * s_msum[c] : 0.0;
                 }
             }
-        } else {
+        } else if constexpr (PairT::kWide) {
             // ---------------- backward (Eq. 4) over the levels ----------------
             int lstop = 0x7fffffff;
             {
@@ -623,10 +711,7 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
         if (tid == 0) q.sflag[si] = (uint32_t)s_flag;
         for (int e = tid; e < nh; e += bd) {
             const int x = hv[e];
-            DistSig z;
-            z.d = ~0ull;
-            z.s = 0.0;
-            ds[x] = z;
+            P.clear(x);
             if (tb) {
                 const long long rb = __ldg(p.off + x), re = __ldg(p.off + x + 1);
                 if (re > rb)
@@ -704,20 +789,27 @@ size_t src_block_bytes(int64_t n, int64_t m, int R, int64_t bcap, int64_t maxlev
            (size_t)chcap * (32 + 8);
 }
 
-// Every pair unreached: distance all ones, sigma zero.
-__global__ void clear_pairs(unsigned long long *ds, size_t npairs) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npairs; i += (size_t)gridDim.x * blockDim.x) {
-        ds[2 * i] = ~0ull;
-        ds[2 * i + 1] = 0ull;  // +0.0
+// Every vertex unreached: 16-byte pairs (distance all ones, sigma zero) or
+// 8-byte words (distance field all ones, count zero).
+__global__ void clear_pairs(unsigned long long *ds, size_t nvert, int layout) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvert; i += (size_t)gridDim.x * blockDim.x) {
+        if (layout == 1) {
+            ds[2 * i] = ~0ull;
+            ds[2 * i + 1] = 0ull;  // +0.0
+        } else {
+            ds[i] = NarrowPairs::kUnreached;
+        }
     }
 }
 
-bc_status clear_src_pairs(bc_graph *g) {
+// Clears the per-block vertex state in the given layout (1 wide, 2 narrow).
+bc_status clear_src_pairs(bc_graph *g, int layout) {
     bcd_workspace &ws = g->ws;
-    const size_t npairs = (size_t)ws.sblocks * (size_t)g->n;
-    clear_pairs<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(ws.sds, npairs);
+    const size_t nvert = (size_t)ws.sblocks * (size_t)g->n;
+    clear_pairs<<<(unsigned)std::max(1, g->num_sms * 8), 256, 0, g->stream>>>(ws.sds, nvert, layout);
     g->launches += 1;
     BCD_CUDA(cudaGetLastError());
+    ws.slayout = layout;
     return BC_OK;
 }
 
@@ -750,13 +842,13 @@ bc_status alloc_src_arrays(bc_graph *g, int blocks) {
     BCD_TRY(dev_alloc(&ws.sch, B * (size_t)ws.schcap));
     BCD_TRY(dev_alloc(&ws.spart, B * (size_t)ws.schcap));
     ws.sblocks = blocks;
-    return clear_src_pairs(g);
+    return clear_src_pairs(g, 1);
 }
 
 bc_status reset_src_state(bc_graph *g) {
     bcd_workspace &ws = g->ws;
     if (!ws.sds) return BC_OK;
-    BCD_TRY(clear_src_pairs(g));
+    BCD_TRY(clear_src_pairs(g, ws.slayout ? ws.slayout : 1));
     BCD_CUDA(cudaMemsetAsync(ws.stb, 0, sizeof(uint32_t) * (size_t)ws.sblocks * (size_t)((g->m + 31) / 32), g->stream));
     if (ws.tag) BCD_CUDA(cudaMemsetAsync(ws.tag, 0xff, sizeof(int32_t) * (size_t)g->n, g->stream));
     return BC_OK;
@@ -786,6 +878,8 @@ void free_src_state(bc_graph *g) {
     ws.sbcap = 0;
     ws.schcap = 0;
     ws.smaxlev = 0;
+    ws.slayout = 0;
+    ws.swide = false;
 }
 
 bool src_kernel_applies(const bc_graph *g, const TravParams &p) {
@@ -801,9 +895,12 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
     const int64_t nsrc = p.ntiles * S;
     const int R = ws.ring;
     const size_t smem = sizeof(uint32_t) * 2 * (size_t)R;
-    int per_sm = 0;
-    BCD_CUDA(cudaFuncSetAttribute(wsrc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wsrc_kernel, threads, smem));
+    int per_sm = 0, per_sm_n = 0;
+    BCD_CUDA(cudaFuncSetAttribute(wsrc_kernel<WidePairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCD_CUDA(cudaFuncSetAttribute(wsrc_kernel<NarrowPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wsrc_kernel<WidePairs>, threads, smem));
+    BCD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_n, wsrc_kernel<NarrowPairs>, threads, smem));
+    per_sm = std::min(per_sm, per_sm_n);
     if (per_sm < 1) return set_error(BC_E_INTERNAL, "weighted source kernel cannot be resident");
     if (ws.sbcap == 0) {
         // queued vertices of one distance of one source: a few times the
@@ -868,12 +965,19 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         q.nsrc = nsrc;
         q.ring = R;
         q.maxlev = ws.smaxlev;
+        // 8-byte words for vertex-scan launches, unless one of this graph
+        // has overflowed them; the Eq. 4 pass needs the 16-byte pairs
+        const int layout = (p.mode == kModeScan && !ws.swide) ? 2 : 1;
+        if (ws.slayout != layout) BCD_TRY(clear_src_pairs(g, layout));
         BCD_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(Counters), g->stream));
         BCD_CUDA(cudaMemsetAsync(ws.snext, 0, sizeof(unsigned long long), g->stream));
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         const bool timed = cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess;
         if (timed) cudaEventRecord(ev0, g->stream);
-        wsrc_kernel<<<(unsigned)ws.sblocks, (unsigned)threads, smem, g->stream>>>(p, q);
+        if (layout == 2)
+            wsrc_kernel<NarrowPairs><<<(unsigned)ws.sblocks, (unsigned)threads, smem, g->stream>>>(p, q);
+        else
+            wsrc_kernel<WidePairs><<<(unsigned)ws.sblocks, (unsigned)threads, smem, g->stream>>>(p, q);
         g->launches += 1;
         g->last_grid = ws.sblocks;
         const cudaError_t le = cudaGetLastError();
@@ -918,6 +1022,11 @@ bc_status run_src_traversal(bc_graph *g, int W, TravParams &p, int *levels_out, 
         if (p.qflags) BCD_CUDA(cudaMemsetAsync(p.qflags, 0, sizeof(uint32_t) * 64, g->stream));
         if (c.err == kDevTimeout) return set_error(BC_E_TIMEOUT, "weighted source kernel: a source ran past the time limit");
         if (c.err == kDevCancelled) return set_error(BC_E_CANCELLED, "traversal: cancelled by bc_cancel");
+        if (c.err == kDevWide) {
+            // a count of 2^40 or a distance of 2^24 - 1: 16-byte pairs from now on
+            ws.swide = true;
+            continue;
+        }
         const size_t before = (size_t)ws.sblocks * src_block_bytes(g->n, g->m, R, ws.sbcap, ws.smaxlev, ws.schcap);
         if (c.err == kDevBucketOverflow) {
             if (ws.sbcap >= ((int64_t)1 << 30)) return set_error(BC_E_OOM, "bucket ring: too many queued vertices at one distance");

@@ -401,6 +401,30 @@ def test_weighted_largest_weights(bcd, kernel, lo):
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
+def test_weighted_large_counts(bcd, kernel):
+    """Layers of 4 vertices, each joined to all 4 of the next by arcs of
+    weight 1, 24 layers: path counts between the first and the
+    last layers reach 4^22 = 2^44, past what the source kernel's 8-byte
+    words hold (2^40), so its vertex-scan launch reruns with 16-byte pairs.
+    Exact scores of the vertex scan (the default for one query vertex) and
+    of the Eq. 4 pull against the oracle; no count reaches 2^53."""
+    L, k = 24, 4
+    arcs = [(l * k + i, (l + 1) * k + j) for l in range(L - 1) for i in range(k) for j in range(k)]
+    g = csr(L * k, arcs, [1] * len(arcs))
+    og = O.Graph.from_csr(g)
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    bcd.bc_set_config(dg, weighted_kernel=kernel)
+    for acc in (4, 1):
+        bcd.bc_set_config(dg, accumulation=acc)
+        for r in (k * 12 + 1, k * 3, k * 20 + 3):
+            got, info = bcd.bc_exact(dg, r)
+            want, _, flags = O.bc_exact(og, r, 0)
+            assert flags == 0 and info["flags"] == 0
+            assert close(got, want), (acc, r, got, want)
+    dg.close()
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
 def test_weighted_growth_paths_closed_forms(bcd, kernel):
     """Capacities that start too small and grow on the rerun.
     - A directed path of 10,000 vertices with weights 1..2 has about 15,000
