@@ -148,14 +148,15 @@ struct TravParams {
     int32_t pad2;
     // vertex scan over several query vertices (columns): column c of the
     // group's distinct query vertices croot[c]; query bit q belongs to column
-    // qcol[q]; rlevq / rsigq [t * 64 + c] = d(croot[c], t) and sigma from it;
+    // qcol[q]; rlevq / rsigq [t * 64 + c] = d(croot[c], t) and sigma from it
+    // (weighted: rdistq / rsigq [t * wcols_stride(ncols) + c]);
     // msum [s * 64 + c] the per-(source, column) sums of the current tile
     int32_t ncols;           // 0 or 1: the one-vertex scan above
     int32_t pad3;
     const int32_t *qcol;     // [64]
     const int32_t *croot;    // [64]
     int32_t *rlevq;          // [n * 64], -1 unreached (unweighted)
-    uint64_t *rdistq;        // [n * 64], UINT64_MAX unreached (weighted)
+    uint64_t *rdistq;        // [n * 64] allocated, UINT64_MAX unreached (weighted)
     double *rsigq;           // [n * 64]
     double *msum;            // [2 * S * 64]: sums, then (weighted) sigma_s(croot[c])
     // reach mode output

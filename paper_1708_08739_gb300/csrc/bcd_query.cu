@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "bcd_common.cuh"
+#include "bcd_wcols.cuh"
 #include "bcd_scan.cuh"
 
 namespace bcd {
@@ -724,7 +725,8 @@ static_assert(kSmallSpecs + 64 * 6 <= kSmallQcol && kSmallCroot + 32 <= kSmallWo
 
 // d(r_c, t) and sigma_{r_c t} for every vertex t and each of several query
 // vertices r_c (the columns): one scan-mode launch over a tile whose slot c
-// holds r_c, kept in rlevq / rsigq [t * 64 + c].
+// holds r_c, kept in rlevq / rsigq [t * 64 + c] (unweighted) or rdistq /
+// rsigq [t * wcols_stride(K) + c] (weighted).
 static bc_status root_traversal_multi(bc_graph *g, const std::vector<int32_t> &roots) {
     bcd_workspace &ws = g->ws;
     cudaStream_t s = g->stream;
@@ -744,7 +746,7 @@ static bc_status root_traversal_multi(bc_graph *g, const std::vector<int32_t> &r
         }
     }
     if (g->weighted)
-        BCD_CUDA(cudaMemsetAsync(ws.rdistq, 0xff, sizeof(uint64_t) * (size_t)g->n * 64, s));
+        BCD_CUDA(cudaMemsetAsync(ws.rdistq, 0xff, sizeof(uint64_t) * (size_t)g->n * wcols_stride(K), s));
     else
         BCD_CUDA(cudaMemsetAsync(ws.rlevq, 0xff, sizeof(int32_t) * (size_t)g->n * 64, s));
     std::vector<int32_t> tsrc(S, -1);

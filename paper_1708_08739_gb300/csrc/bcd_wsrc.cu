@@ -50,6 +50,7 @@
 // request sets the launch's error word; the block leaves, the others stop at
 // their next source, and the host resets the state (and grows what was full).
 #include "bcd_common.cuh"
+#include "bcd_wcols.cuh"
 #include "bcd_device.cuh"
 
 namespace bcd {
@@ -607,9 +608,9 @@ __global__ void __launch_bounds__(kSrcThreads, 1) wsrc_kernel(TravParams p, SrcP
                     y &= y - 1;
                     const unsigned long long dc = s_cd[c];
                     if (dc == PairT::kUnreached) continue;
-                    const unsigned long long rd = p.rdistq[(size_t)t * 64 + c];
+                    const unsigned long long rd = p.rdistq[(size_t)t * wcols_stride(p.ncols) + c];
                     if (rd == 0ull || rd >= dt || dc + rd != dt) continue;
-                    atomicAdd(&s_msum[c], p.rsigq[(size_t)t * 64 + c] / sst);
+                    atomicAdd(&s_msum[c], p.rsigq[(size_t)t * wcols_stride(p.ncols) + c] / sst);
                     st.pairs += 1;
                 }
             }

@@ -37,6 +37,7 @@
 // (the pair dependencies of Eq. 2), with d(r, t) and sigma_rt from an earlier
 // scan-mode launch whose only source is r (kFlagRootOut).
 #include "bcd_common.cuh"
+#include "bcd_wcols.cuh"
 #include "bcd_device.cuh"
 
 namespace bcd {
@@ -458,8 +459,8 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                 const int c = p.hs[e];
                 const size_t iv = ((size_t)v << tl.shift) + c;
                 if (p.ncols >= 2) {
-                    p.rdistq[(size_t)v * 64 + c] = p.dist[iv];
-                    p.rsigq[(size_t)v * 64 + c] = p.sigma[iv];
+                    p.rdistq[(size_t)v * wcols_stride(p.ncols) + c] = p.dist[iv];
+                    p.rsigq[(size_t)v * wcols_stride(p.ncols) + c] = p.sigma[iv];
                 } else {
                     p.rdist[v] = p.dist[iv];
                     p.rsig[v] = p.sigma[iv];
@@ -495,11 +496,11 @@ __global__ void __launch_bounds__(512, 2) wtrav_kernel(TravParams p) {
                         done |= 1ull << c;
                         const int ql = p.qlevel[s * 64 + q];
                         if (ql < 0) continue;
-                        const unsigned long long rd = p.rdistq[(size_t)t * 64 + c];
+                        const unsigned long long rd = p.rdistq[(size_t)t * wcols_stride(p.ncols) + c];
                         if (rd == 0ull || rd >= dk) continue;  // t = r_c, unreached from r_c, or too far
                         if ((unsigned long long)p.lev_dist[ql] + rd != dk) continue;
                         if (sst == 0.0) sst = p.sigma[((size_t)t << tl.shift) + s];
-                        atomicAdd(&p.msum[s * 64 + c], p.rsigq[(size_t)t * 64 + c] / sst);
+                        atomicAdd(&p.msum[s * 64 + c], p.rsigq[(size_t)t * wcols_stride(p.ncols) + c] / sst);
                         ++pairs;
                     }
                 }

@@ -511,6 +511,31 @@ def test_batch_shards_add_up(bcd, er1, nshards):
         bcd.bc_batch_shard(dg, specs, nshards, nshards)
 
 
+@pytest.mark.parametrize("nshards", [1, 3])
+def test_weighted_batch_shards_add_up(bcd, wer, nshards):
+    """bc_batch_shard on a weighted graph (the source kernel, 64-source
+    tiles): exact and sampled queries, the shards' partial scores summed in
+    shard order equal the oracle's."""
+    from paper_1708_08739_gb300 import shard as sh
+    g, og = wer[1]
+    dg = make(bcd, g, weighted_words=1)
+    rs = gg.random_vertices(g.n, 8, 42).tolist()
+    specs = [{"r": r, "kind": bcd.BC_QUERY_EXACT} if i % 2 == 0 else
+             {"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": 500, "seed": 9} for i, r in enumerate(rs)]
+    parts = {}
+    for k in range(nshards):
+        out, _ = bcd.bc_batch_shard(dg, specs, k, nshards)
+        assert all(o["status"] == 0 for o in out)
+        parts[k] = [o["bc"] for o in out]
+    tot = sh.reduce_in_shard_order(parts, nshards, len(specs))
+    for i, s in enumerate(specs):
+        if s["kind"] == bcd.BC_QUERY_EXACT:
+            want = O.bc_exact(og, s["r"], 0)[0]
+        else:
+            want = O.bc_approx(og, s["r"], s["T"], s["seed"], 0)[0]
+        assert close(tot[i], want), (nshards, s, tot[i], want)
+
+
 # ---------------------------------------------------------------- bottom-up levels
 
 @pytest.mark.parametrize("cfg", [{"pull_permille": 1}, {"pull_permille": 1, "tile_words": 1},
