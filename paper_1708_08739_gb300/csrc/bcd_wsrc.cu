@@ -8,21 +8,24 @@
 // them per tile with weights up to 255) is gone, and so is the idle time of
 // every lane waiting there for the slowest chain of the level.
 //
-// State of a block, for its current source s: one 16-byte pair per vertex v,
-// (dist(v), sigma(v)) (distance all ones when unreached; during the Eq. 4
-// pass c(v) = (1 + delta(v)) / sigma(v) replaces sigma in place), the settled
-// vertices in settling order (history) with the start and distance of each
-// distance level, and the bucket ring: R slots (R a power of two above the
-// largest weight) of bcap queued vertices each, with their queued / consumed
-// counters in shared memory.
+// State of a block, for its current source s: one (dist(v), sigma(v)) pair
+// per vertex v, 16 bytes (distance all ones when unreached; during the Eq. 4
+// pass c(v) = (1 + delta(v)) / sigma(v) replaces sigma in place) or, in
+// vertex-scan launches, one 8-byte word (24-bit distance, 40-bit count: half
+// the footprint, so more of it stays in L2; a launch that overflows them
+// reruns on 16-byte pairs); the settled vertices in settling order (history)
+// with the start and distance of each distance level; and the bucket ring: R
+// slots (R a power of two above the largest weight) of bcap queued vertices
+// each, with their queued / consumed counters in shared memory. Eq. 4
+// launches also keep one bit per arc (see src_relax).
 //
 // Sigma rides along the relaxations. Settling u at distance d (its sigma is
 // final: every predecessor on a shortest path sits at a smaller distance and
 // relaxed its arcs in an earlier level), each out-arc (u, v, w) offers the
 // candidate nd = d + w: if nd is below dist(v) the pair becomes (nd,
 // sigma(u)) and v is queued in the slot of nd; if nd equals dist(v),
-// sigma(u) is added. The pair changes by one 16-byte compare-and-swap, so a
-// distance and its path count always move together, and when v settles its
+// sigma(u) is added. The pair changes by one compare-and-swap (128 or 64
+// bits), so a distance and its path count always move together, and when v settles its
 // pair holds its distance with the sum over exactly its tight in-arcs (sigma
 // values are integers: exact in any order below 2^53). Every arc is read
 // once in the forward pass, along its tail's out-row; no in-arc pass.
