@@ -4,7 +4,8 @@ or by a bounded device wait that runs out):
     the call returns BC_E_TIMEOUT, and with the default limit restored the
     same handle answers as the oracle does;
   - bc_cancel from another thread stops a long batch between two tiles
-    (BC_E_CANCELLED), and the handle answers correctly afterwards;
+    (BC_E_CANCELLED), or, on a weighted graph, between two sources of a
+    block, and the handle answers correctly afterwards;
   - an injected allocation failure (the k-th cudaMalloc) returns BC_E_OOM
     from graph creation or from the first query, and the next call, with the
     injection off, matches the oracle.
@@ -104,6 +105,41 @@ def test_cancel_between_tiles(bcd):
     assert box["err"].status == bcd.BC_E_CANCELLED
     # a cancel request made while no call runs is dropped by the next call
     bcd.bc_cancel(dg)
+    r = top[0]
+    want, draws, k, _ = O.bc_approx(og, r, 64, 7, 0)
+    got, info = bcd.bc_approx_T(dg, r, 64, 7)
+    assert info["rv_size"] == k and close(got, want), (got, want)
+
+
+def test_weighted_cancel_between_sources(bcd):
+    """The weighted source kernel checks the cancel request each time a
+    block takes a source: exact queries on the top vertices of weighted
+    R-MAT 18 (seconds of sources), cancelled 0.3 s in; the handle then
+    answers a sampled query as the oracle does."""
+    g = gg.rmat(18, 16, 0.57, 0.19, 0.19, seed=18)
+    g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
+    og = O.Graph.from_csr(g)
+    dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
+    assert bcd.bc_get_config(dg)["weighted_kernel"] == 2
+    top = [int(x) for x in gg.top_inout_vertices(g, 8)]
+    box = {}
+
+    def run():
+        t = time.time()
+        try:
+            box["out"] = bcd.bc_batch(dg, [{"r": r} for r in top])
+        except bcd.BCError as ex:
+            box["err"] = ex
+        box["s"] = time.time() - t
+
+    th = threading.Thread(target=run)
+    th.start()
+    time.sleep(0.3)
+    bcd.bc_cancel(dg)
+    th.join(timeout=300)
+    assert not th.is_alive()
+    assert "err" in box, "the batch finished before the cancel request (%.2f s)" % box.get("s", -1)
+    assert box["err"].status == bcd.BC_E_CANCELLED
     r = top[0]
     want, draws, k, _ = O.bc_approx(og, r, 64, 7, 0)
     got, info = bcd.bc_approx_T(dg, r, 64, 7)
