@@ -295,7 +295,8 @@ def wer():
 WCFGS = [{}, {"weighted_words": 1}, {"weighted_words": 4, "chunk_arcs": 32},
          {"weighted_kernel": 1}, {"weighted_kernel": 1, "weighted_words": 1},
          {"weighted_kernel": 1, "weighted_words": 4, "chunk_arcs": 32},
-         {"weighted_short_row": 2, "chunk_arcs": 32, "block_threads": 128}]
+         {"weighted_short_row": 2, "chunk_arcs": 32, "block_threads": 128},
+         {"weighted_words": 16}, {"weighted_kernel": 1, "weighted_words": 16}]
 
 
 @pytest.mark.parametrize("cfg", WCFGS)
