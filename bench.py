@@ -720,7 +720,8 @@ def run_wprofile_case(args):
     g = gg.rmat(args.case_scale, 16, 0.57, 0.19, 0.19, seed=20)
     g = g.with_weights(gg.uniform_weights(g.m, 1, 255, 3))
     dg = bcd.bc_graph_create(g.n, g.offsets, g.cols, g.weights)
-    bcd.bc_set_config(dg, weighted_words=args.weighted_words, accumulation=args.accumulation or 1)
+    bcd.bc_set_config(dg, weighted_words=args.weighted_words, accumulation=args.accumulation or 1,
+                      weighted_kernel=args.weighted_kernel)
     r = int(gg.top_inout_vertices(g, 1)[0])
     out, info = bcd.bc_batch(dg, [{"r": r, "kind": bcd.BC_QUERY_APPROX_T, "T": args.case_T, "seed": 7}])
     print(json.dumps({"case": "wprofile", "scale": args.case_scale, "r": r, "T": args.case_T, "bc": out[0]["bc"],
@@ -848,6 +849,8 @@ def main():
                          "no JSON bench line")
     ap.add_argument("--case-scale", type=int, default=20, help="R-MAT scale of the wprofile case")
     ap.add_argument("--weighted-words", type=int, default=0, help="weighted tile width (64-source words; 0: default)")
+    ap.add_argument("--weighted-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="wprofile case: 1 the weighted tile kernel, 2 the source kernel (0: the library default, 2)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--case-T", type=int, default=512)
     ap.add_argument("--case-queries", type=int, default=1, help="profile case: query vertices (1: the top vertex)")
