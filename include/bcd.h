@@ -341,8 +341,10 @@ void bc_server_destroy(bc_server *srv);
  *                  2 keeps ascending vertex ids;
  *   blocks_per_sm  resident blocks per SM for tile_words = 4 (1 or 2; 2,
  *                  the default, trades register spills for occupancy);
- *   weighted_words sources per tile of the weighted kernel, in words of 64
- *                  (1, 2, 4, 8 or 16, with n * 64 * weighted_words <= 2^32).
+ *   weighted_words sources per tile of the weighted tile kernel, in words
+ *                  of 64 (1, 2, 4, 8 or 16, with n * 64 * weighted_words <=
+ *                  2^32); on the source kernel only the grouping of the
+ *                  per-query partial sums.
  *                  bc_graph_create picks 4, or less when that does not fit
  *                  in half of the free device memory at about 40 bytes per
  *                  (vertex, source) pair. tile_words applies to unweighted
@@ -362,15 +364,16 @@ void bc_server_destroy(bc_server *srv);
  *                  shortest s-t path: the Bellman criterion), one pass over
  *                  the tile's reached (vertex, source) pairs with no
  *                  per-level barrier, on unweighted and weighted graphs;
- *                  3 the vertex scan for every group of an unweighted graph,
- *                  with its queries at up to 64 distinct vertices r_c: one
- *                  traversal rooted at all of them gives d(r_c, t) and
- *                  sigma_{r_c t} (12 bytes per vertex and column, 64 columns
- *                  allocated on first use), and each tile's pass screens its
- *                  reached (vertex, source) pairs for 8 columns at a time;
- *                  weighted graphs keep 2's choice;
+ *                  3 the vertex scan for every group, with its queries at
+ *                  up to 64 distinct vertices r_c: one traversal rooted at
+ *                  all of them gives d(r_c, t) and sigma_{r_c t} (12 bytes
+ *                  per vertex and column on unweighted graphs, 16 on
+ *                  weighted ones; 64 columns allocated on first use), and
+ *                  each tile's pass (each source's, on the weighted source
+ *                  kernel) screens its reached (vertex, source) pairs for
+ *                  the columns of the queries that need the source;
  *                  4 (default) 2 for one-vertex groups and, for a group
- *                  at several vertices of an unweighted graph, 3 on its
+ *                  at several vertices, 3 on its
  *                  first tile, then for the remaining tiles the scan when
  *                  its terms on that tile, weighted 16 to 1, did not
  *                  outnumber the tight (source, arc) pairs the Eq. 4 push
@@ -389,11 +392,13 @@ void bc_server_destroy(bc_server *srv);
  *                  arc), the others top-down (the frontier pushes sigma
  *                  along its out-arcs); 1..1000, or -1 for top-down only.
  *                  Results are identical either way (sigma sums integers).
- *   weighted_short_row  weighted kernel: a settled (vertex, source) pair
- *                  whose in- and out-rows both have at most this many arcs
- *                  is handled by one lane; longer rows are cut into
- *                  chunk_arcs chunks that a warp takes with lanes over arcs
- *                  (1..1024, default 32).
+ *   weighted_short_row  weighted kernels: a settled vertex (source kernel:
+ *                  whose out-row; tile kernel: a (vertex, source) pair whose
+ *                  in- and out-rows both) has at most this many arcs is
+ *                  handled by the lanes given to it in its level (1 to 32,
+ *                  tile kernel 1 to 8); longer rows are cut into chunk_arcs
+ *                  chunks that a warp takes with lanes over arcs (1..1024,
+ *                  default 32).
  *   timeout_us     limit, in microseconds of wall time, on every wait of a
  *                  traversal kernel at a grid-wide barrier (default
  *                  10,000,000: 10 s), and on the time one block of the
