@@ -232,7 +232,7 @@ bc_status grow_levels(bc_graph *g) {
     return st;
 }
 
-// Distance slab and bucket ring of the weighted kernel. A tile settles each
+// Distance slab and bucket ring of the weighted tile kernel. A tile settles each
 // (vertex, source) pair once, so the history holds up to n * S entries.
 static bc_status build_weighted_state(bc_graph *g);
 
